@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""All-mode sparse MTTKRP benchmark (Gnnz/s and fraction of the HBM roofline).
+
+One step = MTTKRP for every mode of the tensor, back to back, with fixed
+input factors (the paper's metric: time to compute MTTKRP along all modes
+in one iteration, Sec. 5.1), output zero rows and split-row combine
+included, preprocessing excluded.  Default workload: the 3-mode power-law
+tensor 10M x 5M x 2M with 200M nonzeros (Zipf(1.1) over a random
+permutation of each mode), rank 32, fp32 factors; the bf16-factor run is
+reported beside it.  Inputs (2.4 GB of streams per mode) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+    python bench.py [--steps K] [--warmup W] [--workload zipf3] [--impl reference]
+
+Multi-GPU (torchrun): every rank runs an independent replica on its own
+GPU (no collective on the data path); value = all ranks' nonzeros / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "sparse MTTKRP Gnnz/s (all modes, R=32), % of HBM roofline; FP32 vs BF16"
+UNIT = "Gnnz/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="zipf3", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--scale", type=float, default=1.0, help="scale nnz and dims (debug)")
+    ap.add_argument("--segment-items", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- distributed plumbing
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(x: float, pg, device=None) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        import torch
+        t = torch.zeros(1, device=device)
+        pg.all_reduce(t)
+
+
+# --------------------------------------------------------------------------- measurement helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        time.sleep(0.15)
+        self.result = None
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = []
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), f[4:9]))
+            except ValueError:
+                pass
+        if not rows:
+            return
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl[1:]) if v.lower() == "active"})
+        self.result = {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                       "samples": len(rows), "reasons": reasons}
+
+
+def distinct_rows(c):
+    return [int(np.count_nonzero(np.bincount(c.idx[:, n], minlength=c.dims[n]))) for n in range(c.nmodes)]
+
+
+def bytes_model(c, R, sf, U):
+    """Compulsory bytes per mode m: the coordinate/value streams, every distinct
+    input-factor row once, and every output row written once (zero rows included,
+    since the kernel writes them in the same pass)."""
+    N = c.nmodes
+    out = []
+    for m in range(N):
+        b = c.nnz * (4 * (N - 1) + 4)
+        b += sum(U[n] * R * sf for n in range(N) if n != m)
+        b += c.dims[m] * R * 4
+        out.append(b)
+    return out
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2507_15121_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch of the MTTKRP kernel from the committed ncu summary,
+    used only while the kernel sources still hash to the captured version."""
+    path = os.path.join(ROOT, "profiles", f"mttkrp_{workload}_traffic.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch_f32"])
+    except Exception:
+        return None
+
+
+def workload_config(w, args):
+    return {"workload": w.name, "dims": list(w.dims), "nnz": w.nnz, "modes": len(w.dims), "rank": w.rank,
+            "index_dist": [list(d) for d in w.index_dist], "values": list(w.values), "seed": w.seed,
+            "factors": "fp32 U(0,1); bf16 variant rounded from the same draws",
+            "segment_items": args.segment_items or 1024, "l2": "inputs_exceed_l2 (no flush)",
+            "parallelism": "single GPU per rank; ranks run independent replicas"}
+
+
+# --------------------------------------------------------------------------- reference arm (FP64 CPU oracle)
+def run_reference(args, w, world, rank, pg):
+    import oracle
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    # bounded sample: the first M nonzeros of the same seeded draw, sized so the
+    # whole run is about a minute of single-thread oracle work
+    M = int(min(2_000_000, max(20_000, 60e6 / ((W + K) * len(w.dims)))))
+    ws = synth.Workload(w.name, w.dims, min(M, w.nnz), w.index_dist, w.values, w.rank, w.seed)
+    c = synth.make(ws)
+    F = synth.factors(c.dims, w.rank, w.seed)
+    times = []
+    for s in range(W + K):
+        t0 = time.perf_counter()
+        for m in range(c.nmodes):
+            oracle.mttkrp(c.dims, c.idx, c.vals, F, m)
+        if s >= W:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = c.nnz * K / tot / 1e9
+    sample = f"first {c.nnz} nonzeros of {w.name} (all {c.nmodes} modes per step), FP64 single thread"
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": tot / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference", "config": workload_config(w, args),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def time_steps(t, Fd, K, W, torch, stream):
+    """W warm-up steps, then K timed steps; returns (total ms, per-mode kernel ms lists)."""
+    N = t.nmodes
+    outs = [torch.empty((t.dims[m], Fd[0].shape[1]), dtype=torch.float32, device=Fd[0].device) for m in range(N)]
+    for _ in range(W):
+        for m in range(N):
+            t.mttkrp(m, Fd, out=outs[m], stream=stream)
+    torch.cuda.synchronize()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(N)]
+          for _ in range(K)]
+    for row in ev:
+        for a, b in row:
+            a.record(stream)
+            b.record(stream)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    launches0 = None
+    import paper_2507_15121_gb300 as amped
+    launches0 = amped.kernel_launches()
+    start.record(stream)
+    for k in range(K):
+        for m in range(N):
+            t.set_kernel_events(ev[k][m][0], ev[k][m][1])
+            t.mttkrp(m, Fd, out=outs[m], stream=stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    launches = amped.kernel_launches() - launches0
+    total = start.elapsed_time(stop)
+    per_mode = [[ev[k][m][0].elapsed_time(ev[k][m][1]) for k in range(K)] for m in range(N)]
+    return total, per_mode, launches
+
+
+def run_ours(args, w, world, rank, local, pg):
+    import torch
+    import paper_2507_15121_gb300 as amped
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    K, W = args.steps, args.warmup
+    t0 = time.time()
+    c = synth.make(w)
+    F = synth.factors(c.dims, w.rank, w.seed)
+    U = distinct_rows(c)
+    gen_s = time.time() - t0
+    t0 = time.time()
+    t = amped.Tensor(c.dims, c.idx, c.vals, segment_items=args.segment_items)
+    create_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    Fd = [torch.from_numpy(f).to(device) for f in F]
+    peak, peak_kind = peaks()
+
+    barrier(pg, device)
+    with ClockSampler(local) as clk:
+        total, per_mode, launches = time_steps(t, Fd, K, W, torch, stream)
+        if not args.no_bf16:
+            Fb = [f.to(torch.bfloat16) for f in Fd]
+            total_b, per_mode_b, launches_b = time_steps(t, Fb, K, W, torch, stream)
+    barrier(pg, device)
+    total = max_over_ranks(total, pg, device)
+
+    B = bytes_model(c, w.rank, 4, U)
+    kern_ms = [statistics.mean(x) for x in per_mode]
+    achieved = sum(B) / (sum(kern_ms) * 1e-3) / 1e9
+    traffic = recorded_traffic(w.name)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind + " (STREAM-style copy, MEASURED_PEAKS.json)",
+            "kernel": "mttkrp_kernel<float,4,8,2>", "algorithmic_bytes_per_mode": B,
+            "kernel_ms_per_mode": kern_ms}
+    value = world * c.nnz * K / (total * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded Zipf power-law coordinates, U(0,1) values and factors)",
+            "config": workload_config(w, args), "roofline": roof, "gpu_launches": launches,
+            "clocks": getattr(clk, "result", None),
+            "preprocess_s": {"generate": gen_s, "create": create_s}}
+    if not args.no_bf16:
+        Bb = bytes_model(c, w.rank, 2, U)
+        kb = [statistics.mean(x) for x in per_mode_b]
+        ach_b = sum(Bb) / (sum(kb) * 1e-3) / 1e9
+        total_b = max_over_ranks(total_b, pg, device)
+        line["variants"] = {"bf16_factors": {
+            "value": world * c.nnz * K / (total_b * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": total_b / K,
+            "gpu_launches": launches_b,
+            "roofline": {"bound": "hbm", "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
+                         "traffic": None, "kernel": "mttkrp_kernel<bf16,8,4,2>", "algorithmic_bytes_per_mode": Bb,
+                         "kernel_ms_per_mode": kb}}}
+        del Fb
+
+    # end to end through the host-buffer entry point: factors in, outputs out, every step
+    if not args.no_e2e:
+        Fh = [torch.from_numpy(f).pin_memory() for f in F]
+        Oh = [torch.empty((d, w.rank), dtype=torch.float32).pin_memory() for d in c.dims]
+        for _ in range(min(W, 2)):
+            t.mttkrp_all_host(Fh, Oh)
+        Ke = max(1, min(K, 10))
+        barrier(pg, device)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(Ke):
+            t.mttkrp_all_host(Fh, Oh)
+        e2e_s = max_over_ranks(time.perf_counter() - t1, pg, device)
+        line["e2e"] = {"value": world * c.nnz * Ke / e2e_s / 1e9, "unit": UNIT, "steps": Ke,
+                       "h2d_bytes_per_step": int(sum(f.numel() * 4 for f in F)),
+                       "d2h_bytes_per_step": int(sum(o.numel() * 4 for o in Oh)),
+                       "entry": "amped_mttkrp_all_host (pinned host factors and outputs)"}
+        del Fh, Oh
+
+    t.close()
+    del Fd
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        M = min(2_000_000, c.nnz)
+        ci = np.ascontiguousarray(c.idx[:M])
+        cv = np.ascontiguousarray(c.vals[:M])
+        t1 = time.perf_counter()
+        for m in range(c.nmodes):
+            oracle.mttkrp(c.dims, ci, cv, F, m)
+        cpu_s = time.perf_counter() - t1
+        line["cpu_baseline"] = {"value": M / cpu_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {M} nonzeros of {w.name}, all {c.nmodes} modes, FP64 single "
+                                          f"thread ({cpu_s:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    w = synth.WORKLOADS[args.workload].scaled(args.scale)
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, w, world, rank, pg)
+    else:
+        run_ours(args, w, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

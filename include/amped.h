@@ -1,0 +1,176 @@
+/*
+ * amped.h — C ABI of the GB300 sparse MTTKRP library.
+ *
+ * The library computes sparse MTTKRP along every mode of an N-mode COO
+ * tensor (paper Sec. 2.1 Eq. 1: X_(d) times the Khatri-Rao product of the
+ * other factors), which is the bottleneck of CP decomposition, together with
+ * the sampled CP model and its gradient for gradient-based CP completion.
+ * Everything runs on one GPU.  There is no CPU fallback: a call either
+ * enqueues CUDA kernels or returns an error.
+ *
+ * Conventions shared by all entry points
+ *  - Indices are 0-based int32; nnz < 2^31; 1 <= nmodes <= AMPED_MAX_MODES;
+ *    every dims[n] >= 1 and < 2^31.
+ *  - Factors are dense row-major [dims[n]][R] device arrays in fp32, bf16 or
+ *    fp16 (`amped_dtype`), base address aligned to 16 bytes.  Products and
+ *    sums are always fp32; outputs are fp32.
+ *  - Device buffers passed in (factors, outputs, values) are owned by the
+ *    caller and must stay valid until the work enqueued on `stream` is done.
+ *    The handle owns every device copy it builds and frees it in
+ *    amped_tensor_destroy.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream).  Argument errors are detected on the host before
+ *    anything is enqueued and return without side effects; launch errors
+ *    return AMPED_ERR_CUDA.  amped_last_error() describes the last failure
+ *    of the calling thread.
+ *  - A handle may be used from one host thread at a time; calls on the same
+ *    handle that overlap on the GPU (different streams) race on the
+ *    handle's scratch buffers, so serialise them on one stream.
+ */
+#ifndef AMPED_H
+#define AMPED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMPED_MAX_MODES 8
+
+typedef enum {
+    AMPED_OK = 0,
+    AMPED_ERR_INVALID = -1,     /* bad argument (null pointer, size, mode, alignment) */
+    AMPED_ERR_INDEX = -2,       /* a coordinate lies outside its mode's range */
+    AMPED_ERR_OOM = -3,         /* host or device allocation failed */
+    AMPED_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed */
+    AMPED_ERR_UNSUPPORTED = -5, /* rank / dtype / mode count this build has no kernel for */
+    AMPED_ERR_TIMEOUT = -6      /* reserved: a bounded device wait gave up (no kernel waits today) */
+} amped_status;
+
+typedef enum { AMPED_F32 = 0, AMPED_BF16 = 1, AMPED_F16 = 2 } amped_dtype;
+
+/* Options for amped_tensor_create.  Zero-initialise and set what you need;
+ * a field left at 0 takes its default. */
+typedef struct {
+    int32_t segment_items; /* work items (nonzeros + output rows) per segment; default 1024 */
+    int32_t keep_perm;     /* 1 = keep each copy's nonzero permutation on the device (needed by
+                              amped_cp_grad); 2 = do not keep it; 0 = default (keep) */
+    int32_t keep_coo;      /* 1 = keep the coordinates in caller order on the device (needed by
+                              amped_cp_sample); 2 = do not keep; 0 = default (keep) */
+    int32_t max_rank;      /* rank the scratch is first sized for (grown on demand); default 64 */
+    int32_t host_threads;  /* threads for the host reorder; 0 = all available */
+} amped_opts;
+
+typedef struct amped_tensor* amped_tensor_t;
+
+/*
+ * Build the per-mode copies of a COO tensor (paper Sec. 3: one copy of the
+ * tensor per output mode, Sec. 3.1 tensor sharding, Sec. 3.2 inter-shard
+ * partitioning; here the whole tensor is one shard on one GPU).
+ *   nnz      number of nonzeros, 0 <= nnz < 2^31
+ *   nmodes   N, 1..AMPED_MAX_MODES
+ *   dims     host array [N], each >= 1
+ *   idx      host array [nnz][N] int32, 0-based (array-of-structs, caller order)
+ *   vals     host array [nnz] fp32
+ *   opts     NULL for defaults
+ *   out      receives the handle
+ * For every mode d the nonzeros are ordered by i_d (stable), stored as
+ * struct-of-arrays (the N-1 other coordinates and the value), and cut into
+ * segments of at most `segment_items` work items (one item per nonzero and
+ * per output row), so a row longer than a segment is split across segments.
+ * Returns AMPED_ERR_INDEX (and names the first bad nonzero in
+ * amped_last_error) when a coordinate is out of range.  The copies live on
+ * the device that is current when this is called, and every later call on
+ * the handle must run with that device current.  Synchronous: the copies are
+ * on the device when it returns.  Host memory is borrowed only for the
+ * duration of the call.
+ */
+amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
+                                 const float* vals, const amped_opts* opts, amped_tensor_t* out);
+
+/* Free every device and host buffer of the handle (synchronises the device first). NULL is a no-op. */
+amped_status amped_tensor_destroy(amped_tensor_t t);
+
+/* Shape queries (host only). */
+amped_status amped_tensor_info(amped_tensor_t t, int64_t* nnz, int* nmodes, int64_t* dims /* [N] or NULL */);
+
+/*
+ * Mode-`mode` MTTKRP (paper Sec. 3 elementwise computation, Alg. 2):
+ *   out(i, r) = sum over nonzeros x with i_mode = i of val(x) * prod_{n != mode} A_n(i_n, r)
+ *   factors  host array of N device pointers; factors[n] is [dims[n]][R] in `fdtype`;
+ *            factors[mode] is not read and may be NULL
+ *   R        rank, 1..128 for fp32 and 1..256 for bf16/fp16 (R > 32 needs R % 4 == 0 for fp32,
+ *            R % 8 == 0 for 16-bit)
+ *   out      device [dims[mode]][R] fp32, fully overwritten (rows without nonzeros become 0)
+ * Enqueues a scratch reset, the persistent MTTKRP kernel and the split-row combine on `stream`.
+ */
+amped_status amped_mttkrp(amped_tensor_t t, int mode, const void* const* factors, amped_dtype fdtype, int R,
+                          float* out, void* stream);
+
+/* All modes back to back with the same input factors (paper Alg. 1 on one GPU, without the
+ * all-gather): outs[d] receives the mode-d MTTKRP.  outs is a host array of N device pointers. */
+amped_status amped_mttkrp_all(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
+                              float* const* outs, void* stream);
+
+/*
+ * amped_mttkrp_all on HOST buffers: copies the factors host->device into staging owned by the
+ * handle, runs every mode, copies the outputs device->host, and returns when the outputs are on
+ * the host.  factors: host array of N host pointers ([dims[n]][R] in fdtype); outs: host array
+ * of N host pointers ([dims[n]][R] fp32).  Page-locked host memory gives full copy bandwidth.
+ */
+amped_status amped_mttkrp_all_host(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
+                                   float* const* outs, void* stream);
+
+/*
+ * Sampled CP model (paper Sec. 2.1, CPD) at every nonzero, in caller order:
+ *   m_out[k] = sum_r prod_n A_n(i_n(k), r)        (device [nnz] fp32, overwritten)
+ * Needs the handle's caller-order coordinates (opts.keep_coo).
+ */
+amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
+                             float* m_out, void* stream);
+
+/*
+ * Gradient of a loss L(m) of the sampled model, given gvals[k] = dL/dm_k in caller order
+ * (device [nnz] fp32):
+ *   grads[n](i, r) = sum over nonzeros k with i_n(k) = i of gvals[k] * prod_{w != n} A_w(i_w(k), r)
+ * i.e. the mode-n MTTKRP with the values replaced by gvals, for every n.  grads: host array of N
+ * device pointers [dims[n]][R] fp32, overwritten.  Needs opts.keep_perm.
+ */
+amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
+                           const float* gvals, float* const* grads, void* stream);
+
+/*
+ * Host-only planning query: the reorder and segment table that amped_tensor_create builds for
+ * mode `mode`, without touching the GPU (for inspection and tests).  With I = dims[mode] and
+ * S = ceil((I + nnz) / segment_items) (segment_items <= 0 means the default 1024):
+ *   perm       [nnz]   caller index of the k-th nonzero in mode order (stable by i_mode)
+ *   rowptr     [I+1]   row i owns mode-ordered nonzeros rowptr[i] .. rowptr[i+1]-1
+ *   seg_row    [S+1]   rows completed before segment s (merge-path split points)
+ *   seg_nz     [S+1]   nonzeros consumed before segment s
+ *   splits     [S][3]  {row, s_a, s_b}: row straddles segment boundaries s_a..s_b
+ *   nsplit     receives the number of split rows written to `splits`
+ * Any output pointer may be NULL to skip it.  Coordinates are validated as in create.
+ */
+amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode,
+                             int segment_items, int32_t* perm, int32_t* rowptr, int32_t* seg_row, int32_t* seg_nz,
+                             int32_t* splits, int32_t* nsplit);
+
+/* Profiling hook: record `start` / `stop` (cudaEvent_t, may be NULL) on the call's stream
+ * immediately before and after the next MTTKRP kernel launch of this handle; cleared after use. */
+amped_status amped_set_kernel_events(amped_tensor_t t, void* start, void* stop);
+
+/* Number of CUDA kernels this library has launched in this process (all handles). */
+int64_t amped_kernel_launches(void);
+
+/* Message describing the last error returned to the calling thread ("" if none). */
+const char* amped_last_error(void);
+
+/* Library version string. */
+const char* amped_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMPED_H */

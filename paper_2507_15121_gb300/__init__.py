@@ -1,0 +1,19 @@
+"""GB300-native sparse MTTKRP (the hot path of AMPED, arXiv 2507.15121).
+
+All-mode sparse MTTKRP for N-mode COO tensors on one GPU, written as
+hand-tuned sm_103a CUDA behind a C ABI (``include/amped.h``,
+``libamped.so``): a host-side reorder builds one output-row-ordered,
+segmented copy per mode; a persistent kernel whose workers pull segments
+from a device-wide ticket counter streams the coordinates with 128-bit
+loads, gathers factor rows and accumulates each output row in registers.
+Factors may be stored in fp32, bf16 or fp16 (arithmetic in fp32).  A
+``torch.autograd.Function`` gives the sampled CP model with an MTTKRP
+backward for gradient-based CP completion.
+"""
+from ._lib import AmpedError, kernel_launches, version  # noqa: F401
+from .tensor import Tensor, plan_mode  # noqa: F401
+
+try:
+    from .autograd import CPSampled, completion_loss, sampled_model  # noqa: F401
+except ImportError:  # torch missing: only the host planning query is usable
+    pass

@@ -1,0 +1,566 @@
+// api.cu — the C ABI (include/amped.h): handle construction, argument
+// checking, scratch management and kernel dispatch.  Host code only; the
+// kernels live in kernels.cuh (instantiated per dtype) and combine.cu.
+#include <cuda_runtime.h>
+#include <omp.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "amped_internal.h"
+
+namespace amped {
+int launch_mttkrp_f32(int nin, const MttkrpParams& p, int grid_cap, void* st);
+int launch_mttkrp_bf16(int nin, const MttkrpParams& p, int grid_cap, void* st);
+int launch_mttkrp_f16(int nin, const MttkrpParams& p, int grid_cap, void* st);
+int launch_sample_f32(const SampleParams& p, void* st);
+int launch_sample_bf16(const SampleParams& p, void* st);
+int launch_sample_f16(const SampleParams& p, void* st);
+int vec_f32(int R);
+int vec_bf16(int R);
+int vec_f16(int R);
+}  // namespace amped
+
+using namespace amped;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_allocs{0};
+
+amped_status fail(amped_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+amped_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? AMPED_ERR_OOM : AMPED_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+// Host-side fault injection for testing clean-up paths: AMPED_FAULT=alloc:K
+// makes the K-th device allocation of the process (1-based) report failure.
+int64_t fault_alloc_at() {
+    static const int64_t at = [] {
+        const char* s = std::getenv("AMPED_FAULT");
+        if (!s || std::strncmp(s, "alloc:", 6) != 0) return int64_t(0);
+        return (int64_t)std::atoll(s + 6);
+    }();
+    return at;
+}
+
+size_t esize(amped_dtype dt) { return dt == AMPED_F32 ? 4 : 2; }
+
+int kernel_vec(amped_dtype dt, int R) {
+    switch (dt) {
+        case AMPED_F32: return vec_f32(R);
+        case AMPED_BF16: return vec_bf16(R);
+        case AMPED_F16: return vec_f16(R);
+    }
+    return 0;
+}
+
+struct DevMode {
+    int64_t I = 0;
+    int32_t S = 0, nsplit = 0, ntask = 0, nmulti = 0;
+    int32_t* rowptr = nullptr;
+    int32_t* idx = nullptr;  // N-1 streams of `stride` elements
+    float* val = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* seg = nullptr;   // seg_row [S+1], then seg_nz [S+1]
+    int32_t* table = nullptr; // tasks [4*ntask], split_info [2*(nsplit+1)], multi [nmulti]
+};
+
+}  // namespace
+
+struct amped_tensor {
+    int N = 0;
+    int64_t nnz = 0;
+    int64_t dims[AMPED_MAX_MODES] = {};
+    int device = 0;
+    int64_t stride = 0;  // elements per stream array, slack included
+    DevMode m[AMPED_MAX_MODES];
+    int32_t* coo = nullptr;  // caller-order coordinates, N streams of `stride`
+    float* part = nullptr;   // [maxS][2][rcap]
+    double* tsum = nullptr;  // [maxTask][rcap]
+    int* queue = nullptr;
+    int32_t maxS = 0, maxTask = 0, rcap = 0;
+    void* ev_start = nullptr;
+    void* ev_stop = nullptr;
+    void* stage_fac[AMPED_MAX_MODES] = {};
+    size_t stage_fac_bytes[AMPED_MAX_MODES] = {};
+    float* stage_out[AMPED_MAX_MODES] = {};
+    size_t stage_out_bytes[AMPED_MAX_MODES] = {};
+    std::vector<void*> allocs;
+
+    cudaError_t dalloc(void** p, size_t bytes) {
+        *p = nullptr;
+        const int64_t n = ++g_allocs;
+        const int64_t f = fault_alloc_at();
+        if (f > 0 && n == f) return cudaErrorMemoryAllocation;
+        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+        if (e == cudaSuccess) allocs.push_back(*p);
+        return e;
+    }
+    void dfree(void* p) {
+        if (!p) return;
+        auto it = std::find(allocs.begin(), allocs.end(), p);
+        if (it != allocs.end()) allocs.erase(it);
+        cudaFree(p);
+    }
+    ~amped_tensor() {
+        for (void* p : allocs) cudaFree(p);
+    }
+};
+
+namespace {
+
+template <class T>
+cudaError_t upload(amped_tensor* t, T** dst, const T* src, size_t n, size_t cap) {
+    cudaError_t e = t->dalloc(reinterpret_cast<void**>(dst), cap * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (cap > n) e = cudaMemset(*dst + n, 0, (cap - n) * sizeof(T));
+    if (e == cudaSuccess && n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// Scratch for the split-row partials, sized for rank R.
+amped_status ensure_scratch(amped_tensor* t, int R) {
+    if (R <= t->rcap && t->queue) return AMPED_OK;
+    const int rc = std::max(R, t->rcap);
+    cudaError_t e;
+    if (!t->queue && (e = t->dalloc(reinterpret_cast<void**>(&t->queue), 64 * sizeof(int))) != cudaSuccess)
+        return cuda_fail(e, "scratch allocation");
+    cudaDeviceSynchronize();  // scratch may still be in use by earlier work on any stream
+    t->dfree(t->part);
+    t->dfree(t->tsum);
+    t->part = nullptr;
+    t->tsum = nullptr;
+    t->rcap = 0;
+    if ((e = t->dalloc(reinterpret_cast<void**>(&t->part), (size_t)t->maxS * 2 * rc * sizeof(float))) !=
+        cudaSuccess)
+        return cuda_fail(e, "scratch allocation");
+    if ((e = t->dalloc(reinterpret_cast<void**>(&t->tsum), (size_t)t->maxTask * rc * sizeof(double))) !=
+        cudaSuccess)
+        return cuda_fail(e, "scratch allocation");
+    t->rcap = rc;
+    return AMPED_OK;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+amped_status check_call(amped_tensor* t, const void* const* factors, amped_dtype fdtype, int R, int skip_mode,
+                        int* vec) {
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (!factors) return fail(AMPED_ERR_INVALID, "factor pointer array is NULL");
+    if (fdtype != AMPED_F32 && fdtype != AMPED_BF16 && fdtype != AMPED_F16)
+        return fail(AMPED_ERR_INVALID, "unknown factor dtype %d", (int)fdtype);
+    if (R < 1) return fail(AMPED_ERR_INVALID, "rank R=%d must be >= 1", R);
+    *vec = kernel_vec(fdtype, R);
+    if (*vec == 0)
+        return fail(AMPED_ERR_UNSUPPORTED, "no kernel for rank R=%d with %s factors", R,
+                    fdtype == AMPED_F32 ? "fp32" : "16-bit");
+    const size_t al = (size_t)*vec * esize(fdtype);
+    for (int n = 0; n < t->N; ++n) {
+        if (n == skip_mode) continue;
+        if (!factors[n]) return fail(AMPED_ERR_INVALID, "factor %d is NULL", n);
+        if (!aligned(factors[n], al)) return fail(AMPED_ERR_INVALID, "factor %d is not %zu-byte aligned", n, al);
+    }
+    if (t->N < 2 && skip_mode >= 0) return AMPED_OK;
+    if (t->N - 1 > 3 && skip_mode >= 0)
+        return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 4 modes, tensor has %d", t->N);
+    return AMPED_OK;
+}
+
+// One mode: reset the ticket counter, run the persistent kernel, combine split rows.
+amped_status run_mode(amped_tensor* t, int mode, const void* const* factors, amped_dtype fdtype, int R, int vec,
+                      float* out, const float* gval, cudaStream_t st) {
+    const DevMode& dm = t->m[mode];
+    if (!out) return fail(AMPED_ERR_INVALID, "output for mode %d is NULL", mode);
+    if (!aligned(out, vec > 1 ? 16 : 4)) return fail(AMPED_ERR_INVALID, "output for mode %d is misaligned", mode);
+    amped_status s = ensure_scratch(t, R);
+    if (s != AMPED_OK) return s;
+    if (t->N == 1) {  // no input modes: the product is empty, out(i,r) = sum of the row's values
+        return fail(AMPED_ERR_UNSUPPORTED, "single-mode tensors have no MTTKRP kernel");
+    }
+    cudaError_t e = cudaMemsetAsync(t->queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    MttkrpParams p{};
+    p.rowptr = dm.rowptr;
+    int nin = 0;
+    for (int n = 0; n < t->N; ++n) {
+        if (n == mode) continue;
+        p.idx[nin] = dm.idx + (size_t)nin * t->stride;
+        p.fac[nin] = factors[n];
+        ++nin;
+    }
+    p.val = dm.val;
+    p.perm = gval ? dm.perm : nullptr;
+    p.gval = gval;
+    p.seg_row = dm.seg;
+    p.seg_nz = dm.seg + dm.S + 1;
+    p.out = out;
+    p.part = t->part;
+    p.queue = t->queue;
+    p.I = (int32_t)dm.I;
+    p.S = dm.S;
+    p.R = R;
+    p.nnz = (int32_t)t->nnz;
+    if (t->ev_start) cudaEventRecord(static_cast<cudaEvent_t>(t->ev_start), st);
+    int rc;
+    switch (fdtype) {
+        case AMPED_F32: rc = launch_mttkrp_f32(nin, p, 0, st); break;
+        case AMPED_BF16: rc = launch_mttkrp_bf16(nin, p, 0, st); break;
+        default: rc = launch_mttkrp_f16(nin, p, 0, st); break;
+    }
+    if (t->ev_stop) cudaEventRecord(static_cast<cudaEvent_t>(t->ev_stop), st);
+    t->ev_start = t->ev_stop = nullptr;
+    if (rc != 0) return cuda_fail((cudaError_t)rc, "MTTKRP kernel launch");
+    ++g_launches;
+    CombineParams c{};
+    c.tasks = dm.table;
+    c.split_info = dm.table + 4 * (size_t)dm.ntask;
+    c.multi = c.split_info + 2 * ((size_t)dm.nsplit + 1);
+    c.part = t->part;
+    c.tsum = t->tsum;
+    c.out = out;
+    c.ntask = dm.ntask;
+    c.nmulti = dm.nmulti;
+    c.R = R;
+    int launched = 0;
+    rc = launch_combine(c, st, &launched);
+    g_launches += launched;
+    if (rc != 0) return cuda_fail((cudaError_t)rc, "split-row combine launch");
+    return AMPED_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* amped_version(void) { return "amped-gb300 0.1 (sm_103a)"; }
+
+const char* amped_last_error(void) { return g_err.c_str(); }
+
+int64_t amped_kernel_launches(void) { return g_launches.load(); }
+
+amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
+                                 const float* vals, const amped_opts* opts, amped_tensor_t* out) {
+    g_err.clear();
+    if (!out) return fail(AMPED_ERR_INVALID, "output handle pointer is NULL");
+    *out = nullptr;
+    if (nmodes < 1 || nmodes > AMPED_MAX_MODES)
+        return fail(AMPED_ERR_INVALID, "nmodes=%d outside 1..%d", nmodes, AMPED_MAX_MODES);
+    if (nnz < 0 || nnz > (int64_t)INT32_MAX - 4 * kPad)
+        return fail(AMPED_ERR_INVALID, "nnz=%lld outside 0..2^31-%d", (long long)nnz, 4 * kPad);
+    if (!dims) return fail(AMPED_ERR_INVALID, "dims is NULL");
+    for (int n = 0; n < nmodes; ++n)
+        if (dims[n] < 1 || dims[n] > (int64_t)INT32_MAX - 4 * kPad)
+            return fail(AMPED_ERR_INVALID, "dims[%d]=%lld outside 1..2^31-%d", n, (long long)dims[n], 4 * kPad);
+    if (nnz > 0 && (!idx || !vals)) return fail(AMPED_ERR_INVALID, "idx or vals is NULL");
+    int items = 1024, threads = 0, max_rank = 64;
+    bool keep_perm = true, keep_coo = true;
+    if (opts) {
+        if (opts->segment_items < 0 || opts->max_rank < 0 || opts->host_threads < 0)
+            return fail(AMPED_ERR_INVALID, "negative option");
+        if (opts->segment_items > 0) items = opts->segment_items;
+        if (opts->max_rank > 0) max_rank = opts->max_rank;
+        threads = opts->host_threads;
+        keep_perm = opts->keep_perm != 2;
+        keep_coo = opts->keep_coo != 2;
+    }
+    const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, threads);
+    if (bad >= 0) {
+        std::string c;
+        for (int n = 0; n < nmodes; ++n) c += (n ? "," : "") + std::to_string(idx[bad * nmodes + n]);
+        return fail(AMPED_ERR_INDEX, "nonzero %lld has coordinate (%s) outside dims", (long long)bad, c.c_str());
+    }
+
+    amped_tensor* t = new (std::nothrow) amped_tensor;
+    if (!t) return fail(AMPED_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&t->device);
+    t->N = nmodes;
+    t->nnz = nnz;
+    for (int n = 0; n < nmodes; ++n) t->dims[n] = dims[n];
+    t->stride = ((nnz + kPad) + 63) / 64 * 64;
+    const size_t stride = (size_t)t->stride;
+
+    auto bail = [&](amped_status s) {
+        delete t;
+        return s;
+    };
+    HostBuf<int32_t> col;
+    HostBuf<float> fcol;
+    if (!col.alloc(stride) || !fcol.alloc(stride)) return bail(fail(AMPED_ERR_OOM, "host allocation failed"));
+    cudaError_t e;
+    for (int mode = 0; mode < nmodes; ++mode) {
+        HostMode hm;
+        if (!sort_mode(nnz, nmodes, dims, idx, mode, threads, hm) || !cut_segments(hm, items))
+            return bail(fail(AMPED_ERR_OOM, "host allocation failed in the reorder of mode %d", mode));
+        DevMode& dm = t->m[mode];
+        dm.I = hm.I;
+        dm.S = hm.S;
+        dm.nsplit = hm.nsplit;
+        dm.ntask = hm.ntask;
+        dm.nmulti = hm.nmulti;
+        if ((e = upload(t, &dm.rowptr, hm.rowptr.p, (size_t)hm.I + 1, (size_t)hm.I + 1 + kPad)) != cudaSuccess)
+            return bail(cuda_fail(e, "device copy of the row pointers"));
+        if (nmodes > 1) {
+            if ((e = t->dalloc(reinterpret_cast<void**>(&dm.idx), (size_t)(nmodes - 1) * stride * 4)) != cudaSuccess)
+                return bail(cuda_fail(e, "device copy of the coordinates"));
+            int slot = 0;
+            for (int n = 0; n < nmodes; ++n) {
+                if (n == mode) continue;
+                gather_column(hm, nmodes, idx, n, col.p, threads);
+                std::memset(col.p + nnz, 0, (stride - (size_t)nnz) * 4);
+                if ((e = cudaMemcpy(dm.idx + (size_t)slot * stride, col.p, stride * 4, cudaMemcpyHostToDevice)) !=
+                    cudaSuccess)
+                    return bail(cuda_fail(e, "device copy of the coordinates"));
+                ++slot;
+            }
+        }
+        gather_values(hm, vals, fcol.p, threads);
+        std::memset(fcol.p + nnz, 0, (stride - (size_t)nnz) * 4);
+        if ((e = upload(t, &dm.val, fcol.p, stride, stride)) != cudaSuccess)
+            return bail(cuda_fail(e, "device copy of the values"));
+        if (keep_perm && (e = upload(t, &dm.perm, hm.perm.p, (size_t)nnz, stride)) != cudaSuccess)
+            return bail(cuda_fail(e, "device copy of the permutation"));
+        std::vector<int32_t> seg((size_t)2 * (hm.S + 1));
+        std::memcpy(seg.data(), hm.seg_row.p, (size_t)(hm.S + 1) * 4);
+        std::memcpy(seg.data() + hm.S + 1, hm.seg_nz.p, (size_t)(hm.S + 1) * 4);
+        if ((e = upload(t, &dm.seg, seg.data(), seg.size(), seg.size())) != cudaSuccess)
+            return bail(cuda_fail(e, "device copy of the segment table"));
+        std::vector<int32_t> table((size_t)4 * hm.ntask + 2 * ((size_t)hm.nsplit + 1) + hm.nmulti);
+        if (hm.ntask) std::memcpy(table.data(), hm.tasks.p, (size_t)4 * hm.ntask * 4);
+        std::memcpy(table.data() + 4 * (size_t)hm.ntask, hm.split_info.p, 2 * ((size_t)hm.nsplit + 1) * 4);
+        if (hm.nmulti)
+            std::memcpy(table.data() + 4 * (size_t)hm.ntask + 2 * ((size_t)hm.nsplit + 1), hm.multi.p,
+                        (size_t)hm.nmulti * 4);
+        if ((e = upload(t, &dm.table, table.data(), table.size(), table.size())) != cudaSuccess)
+            return bail(cuda_fail(e, "device copy of the combine table"));
+        t->maxS = std::max(t->maxS, hm.S);
+        t->maxTask = std::max(t->maxTask, hm.ntask);
+    }
+    if (keep_coo) {
+        if ((e = t->dalloc(reinterpret_cast<void**>(&t->coo), (size_t)nmodes * stride * 4)) != cudaSuccess)
+            return bail(cuda_fail(e, "device copy of the caller-order coordinates"));
+        for (int n = 0; n < nmodes; ++n) {
+            caller_column(nnz, nmodes, idx, n, col.p, threads);
+            std::memset(col.p + nnz, 0, (stride - (size_t)nnz) * 4);
+            if ((e = cudaMemcpy(t->coo + (size_t)n * stride, col.p, stride * 4, cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+                return bail(cuda_fail(e, "device copy of the caller-order coordinates"));
+        }
+    }
+    amped_status s = ensure_scratch(t, max_rank);
+    if (s != AMPED_OK) return bail(s);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(cuda_fail(e, "tensor create"));
+    *out = t;
+    return AMPED_OK;
+}
+
+amped_status amped_tensor_destroy(amped_tensor_t t) {
+    g_err.clear();
+    if (!t) return AMPED_OK;
+    cudaDeviceSynchronize();
+    delete t;
+    return AMPED_OK;
+}
+
+amped_status amped_tensor_info(amped_tensor_t t, int64_t* nnz, int* nmodes, int64_t* dims) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (nnz) *nnz = t->nnz;
+    if (nmodes) *nmodes = t->N;
+    if (dims)
+        for (int n = 0; n < t->N; ++n) dims[n] = t->dims[n];
+    return AMPED_OK;
+}
+
+amped_status amped_mttkrp(amped_tensor_t t, int mode, const void* const* factors, amped_dtype fdtype, int R,
+                          float* out, void* stream) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (mode < 0 || mode >= t->N) return fail(AMPED_ERR_INVALID, "mode %d outside 0..%d", mode, t->N - 1);
+    int vec = 0;
+    amped_status s = check_call(t, factors, fdtype, R, mode, &vec);
+    if (s != AMPED_OK) return s;
+    return run_mode(t, mode, factors, fdtype, R, vec, out, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+amped_status amped_mttkrp_all(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
+                              float* const* outs, void* stream) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (!outs) return fail(AMPED_ERR_INVALID, "output pointer array is NULL");
+    int vec = 0;
+    amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
+    if (s != AMPED_OK) return s;
+    if (t->N - 1 > 3) return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 4 modes");
+    for (int n = 0; n < t->N; ++n)
+        if (!outs[n]) return fail(AMPED_ERR_INVALID, "output for mode %d is NULL", n);
+    for (int n = 0; n < t->N; ++n) {
+        s = run_mode(t, n, factors, fdtype, R, vec, outs[n], nullptr, static_cast<cudaStream_t>(stream));
+        if (s != AMPED_OK) return s;
+    }
+    return AMPED_OK;
+}
+
+amped_status amped_mttkrp_all_host(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
+                                   float* const* outs, void* stream) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (!outs || !factors) return fail(AMPED_ERR_INVALID, "factor or output pointer array is NULL");
+    int vec = 0;
+    // host pointers: check everything except device alignment, which the staging provides
+    const void* dummy[AMPED_MAX_MODES];
+    for (int n = 0; n < t->N; ++n) {
+        if (!factors[n] || !outs[n]) return fail(AMPED_ERR_INVALID, "host buffer %d is NULL", n);
+        dummy[n] = reinterpret_cast<const void*>(uintptr_t(256));
+    }
+    amped_status s = check_call(t, dummy, fdtype, R, -1, &vec);
+    if (s != AMPED_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    const void* dfac[AMPED_MAX_MODES];
+    float* dout[AMPED_MAX_MODES];
+    for (int n = 0; n < t->N; ++n) {
+        const size_t fb = (size_t)t->dims[n] * R * esize(fdtype), ob = (size_t)t->dims[n] * R * 4;
+        if (t->stage_fac_bytes[n] < fb) {
+            cudaStreamSynchronize(st);
+            t->dfree(t->stage_fac[n]);
+            t->stage_fac_bytes[n] = 0;
+            if ((e = t->dalloc(&t->stage_fac[n], fb)) != cudaSuccess) return cuda_fail(e, "staging allocation");
+            t->stage_fac_bytes[n] = fb;
+        }
+        if (t->stage_out_bytes[n] < ob) {
+            cudaStreamSynchronize(st);
+            t->dfree(t->stage_out[n]);
+            t->stage_out_bytes[n] = 0;
+            if ((e = t->dalloc(reinterpret_cast<void**>(&t->stage_out[n]), ob)) != cudaSuccess)
+                return cuda_fail(e, "staging allocation");
+            t->stage_out_bytes[n] = ob;
+        }
+        if ((e = cudaMemcpyAsync(t->stage_fac[n], factors[n], fb, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "factor upload");
+        dfac[n] = t->stage_fac[n];
+        dout[n] = t->stage_out[n];
+    }
+    for (int n = 0; n < t->N; ++n) {
+        s = run_mode(t, n, dfac, fdtype, R, vec, dout[n], nullptr, st);
+        if (s != AMPED_OK) return s;
+    }
+    for (int n = 0; n < t->N; ++n) {
+        const size_t ob = (size_t)t->dims[n] * R * 4;
+        if ((e = cudaMemcpyAsync(outs[n], dout[n], ob, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(e, "output download");
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "host MTTKRP");
+    return AMPED_OK;
+}
+
+amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R, float* m_out,
+                             void* stream) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (!t->coo) return fail(AMPED_ERR_INVALID, "handle was created without caller-order coordinates (keep_coo)");
+    int vec = 0;
+    amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
+    if (s != AMPED_OK) return s;
+    if (t->N < 2 || t->N > 4) return fail(AMPED_ERR_UNSUPPORTED, "sampled-model kernels are built for 2 to 4 modes");
+    if (t->nnz == 0) return AMPED_OK;
+    if (!m_out || !aligned(m_out, 16)) return fail(AMPED_ERR_INVALID, "m_out is NULL or not 16-byte aligned");
+    SampleParams p{};
+    for (int n = 0; n < t->N; ++n) {
+        p.idx[n] = t->coo + (size_t)n * t->stride;
+        p.fac[n] = factors[n];
+    }
+    p.m = m_out;
+    p.nnz = (int32_t)t->nnz;
+    p.R = R;
+    p.nmodes = t->N;
+    int rc;
+    switch (fdtype) {
+        case AMPED_F32: rc = launch_sample_f32(p, stream); break;
+        case AMPED_BF16: rc = launch_sample_bf16(p, stream); break;
+        default: rc = launch_sample_f16(p, stream); break;
+    }
+    if (rc != 0) return cuda_fail((cudaError_t)rc, "sampled-model kernel launch");
+    ++g_launches;
+    return AMPED_OK;
+}
+
+amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
+                           const float* gvals, float* const* grads, void* stream) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (!grads) return fail(AMPED_ERR_INVALID, "gradient pointer array is NULL");
+    if (t->nnz > 0 && !gvals) return fail(AMPED_ERR_INVALID, "gvals is NULL");
+    if (t->N > 1 && !t->m[0].perm && t->nnz > 0)
+        return fail(AMPED_ERR_INVALID, "handle was created without permutations (keep_perm)");
+    int vec = 0;
+    amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
+    if (s != AMPED_OK) return s;
+    if (t->N - 1 > 3) return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 4 modes");
+    for (int n = 0; n < t->N; ++n)
+        if (!grads[n]) return fail(AMPED_ERR_INVALID, "gradient %d is NULL", n);
+    for (int n = 0; n < t->N; ++n) {
+        s = run_mode(t, n, factors, fdtype, R, vec, grads[n], t->nnz ? gvals : nullptr,
+                     static_cast<cudaStream_t>(stream));
+        if (s != AMPED_OK) return s;
+    }
+    return AMPED_OK;
+}
+
+amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode,
+                             int segment_items, int32_t* perm, int32_t* rowptr, int32_t* seg_row, int32_t* seg_nz,
+                             int32_t* splits, int32_t* nsplit) {
+    g_err.clear();
+    if (nmodes < 1 || nmodes > AMPED_MAX_MODES || !dims || nnz < 0 || nnz > (int64_t)INT32_MAX - 4 * kPad)
+        return fail(AMPED_ERR_INVALID, "bad tensor shape");
+    if (mode < 0 || mode >= nmodes) return fail(AMPED_ERR_INVALID, "mode %d outside 0..%d", mode, nmodes - 1);
+    for (int n = 0; n < nmodes; ++n)
+        if (dims[n] < 1 || dims[n] > (int64_t)INT32_MAX - 4 * kPad)
+            return fail(AMPED_ERR_INVALID, "dims[%d]=%lld out of range", n, (long long)dims[n]);
+    if (nnz > 0 && !idx) return fail(AMPED_ERR_INVALID, "idx is NULL");
+    const int items = segment_items > 0 ? segment_items : 1024;
+    const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, 0);
+    if (bad >= 0) return fail(AMPED_ERR_INDEX, "nonzero %lld has a coordinate outside dims", (long long)bad);
+    HostMode hm;
+    if (!sort_mode(nnz, nmodes, dims, idx, mode, 0, hm) || !cut_segments(hm, items))
+        return fail(AMPED_ERR_OOM, "host allocation failed");
+    if (perm && nnz) std::memcpy(perm, hm.perm.p, (size_t)nnz * 4);
+    if (rowptr) std::memcpy(rowptr, hm.rowptr.p, ((size_t)hm.I + 1) * 4);
+    if (seg_row) std::memcpy(seg_row, hm.seg_row.p, ((size_t)hm.S + 1) * 4);
+    if (seg_nz) std::memcpy(seg_nz, hm.seg_nz.p, ((size_t)hm.S + 1) * 4);
+    if (splits)
+        for (int32_t j = 0; j < hm.nsplit; ++j) {
+            splits[3 * j] = hm.splits[(size_t)j].row;
+            splits[3 * j + 1] = hm.splits[(size_t)j].s_a;
+            splits[3 * j + 2] = hm.splits[(size_t)j].s_b;
+        }
+    if (nsplit) *nsplit = hm.nsplit;
+    return AMPED_OK;
+}
+
+amped_status amped_set_kernel_events(amped_tensor_t t, void* start, void* stop) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    t->ev_start = start;
+    t->ev_stop = stop;
+    return AMPED_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,218 @@
+// reorder.cpp — host preprocessing: per-mode output-row order and the
+// segment table (paper Sec. 3.1 tensor sharding, Sec. 3.2 inter-shard
+// partitioning, Sec. 4.2 partition-to-threadblock mapping).
+//
+// The paper groups all nonzeros sharing an output index into one shard so no
+// two GPUs update the same row, and cuts each shard into equal-size
+// partitions, one per threadblock, with atomics between them.  On one GPU the
+// whole tensor is one shard; it is ordered by the output coordinate (a stable
+// counting sort) and cut into segments of equal *work*: the merge-path split
+// of the sequence "nonzeros of row 0, end of row 0, nonzeros of row 1, ..."
+// into pieces of `items` items.  A segment therefore holds at most `items`
+// nonzeros and at most `items` row ends, so empty rows (which must still be
+// written as zero) and rows longer than a segment are both balanced.  Rows
+// that straddle a segment boundary are the only ones written by more than one
+// segment; they are listed as split rows and combined deterministically.
+#include <omp.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "amped_internal.h"
+
+namespace amped {
+
+template <class T>
+bool HostBuf<T>::alloc(size_t count) {
+    release();
+    p = static_cast<T*>(std::malloc(std::max<size_t>(count, 1) * sizeof(T)));
+    n = p ? count : 0;
+    return p != nullptr;
+}
+template <class T>
+void HostBuf<T>::release() {
+    std::free(p);
+    p = nullptr;
+    n = 0;
+}
+template struct HostBuf<int32_t>;
+template struct HostBuf<int64_t>;
+template struct HostBuf<SplitRow>;
+template struct HostBuf<float>;
+
+static int nthreads(int threads) { return threads > 0 ? threads : omp_get_max_threads(); }
+
+int64_t find_bad_index(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int threads) {
+    int64_t first = -1;
+    const int T = nthreads(threads);
+#pragma omp parallel num_threads(T)
+    {
+        int64_t mine = -1;
+#pragma omp for schedule(static)
+        for (int64_t k = 0; k < nnz; ++k) {
+            if (mine >= 0) continue;
+            for (int n = 0; n < nmodes; ++n) {
+                int32_t c = idx[k * nmodes + n];
+                if (c < 0 || c >= dims[n]) {
+                    mine = k;
+                    break;
+                }
+            }
+        }
+#pragma omp critical
+        if (mine >= 0 && (first < 0 || mine < first)) first = mine;
+    }
+    return first;
+}
+
+bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, int threads,
+               HostMode& hm) {
+    const int64_t I = dims[mode];
+    hm.mode = mode;
+    hm.I = I;
+    hm.nnz = nnz;
+    if (!hm.perm.alloc((size_t)nnz) || !hm.rowptr.alloc((size_t)I + 1)) return false;
+    const int T = nthreads(threads);
+
+    // level 1: bucket by the high bits of the key, at most 2^16 buckets
+    int bits = 0;
+    while ((int64_t(1) << bits) < I) ++bits;
+    const int shift = bits > 16 ? bits - 16 : 0;
+    const int64_t B = ((I - 1) >> shift) + 1;
+    std::vector<int64_t> hist((size_t)T * (size_t)B, 0);
+    HostBuf<int32_t> tmp;
+    if (!tmp.alloc((size_t)nnz)) return false;
+    auto key = [&](int64_t k) -> int64_t { return idx[k * nmodes + mode]; };
+#pragma omp parallel num_threads(T)
+    {
+        const int t = omp_get_thread_num();
+        const int64_t lo = nnz * t / T, hi = nnz * (t + 1) / T;
+        int64_t* h = hist.data() + (size_t)t * B;
+        for (int64_t k = lo; k < hi; ++k) ++h[key(k) >> shift];
+    }
+    // exclusive scan in (bucket, thread) order keeps the scatter stable
+    std::vector<int64_t> bstart((size_t)B + 1);
+    int64_t run = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        bstart[b] = run;
+        for (int t = 0; t < T; ++t) {
+            int64_t c = hist[(size_t)t * B + b];
+            hist[(size_t)t * B + b] = run;
+            run += c;
+        }
+    }
+    bstart[B] = run;
+#pragma omp parallel num_threads(T)
+    {
+        const int t = omp_get_thread_num();
+        const int64_t lo = nnz * t / T, hi = nnz * (t + 1) / T;
+        int64_t* off = hist.data() + (size_t)t * B;
+        for (int64_t k = lo; k < hi; ++k) tmp[(size_t)off[key(k) >> shift]++] = (int32_t)k;
+    }
+    // level 2: stable counting sort of each bucket by the low bits; fills rowptr
+    const int64_t span = int64_t(1) << shift;
+#pragma omp parallel num_threads(T)
+    {
+        std::vector<int64_t> cnt((size_t)span + 1);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t b = 0; b < B; ++b) {
+            const int64_t k0 = bstart[b], k1 = bstart[b + 1];
+            const int64_t key0 = b << shift, nkeys = std::min(span, I - key0);
+            std::fill(cnt.begin(), cnt.begin() + nkeys + 1, 0);
+            for (int64_t j = k0; j < k1; ++j) ++cnt[(size_t)(key(tmp[j]) - key0) + 1];
+            for (int64_t x = 0; x < nkeys; ++x) {
+                cnt[(size_t)x + 1] += cnt[(size_t)x];
+                hm.rowptr[(size_t)(key0 + x)] = (int32_t)(k0 + cnt[(size_t)x]);
+            }
+            for (int64_t j = k0; j < k1; ++j) {
+                const int32_t c = tmp[j];
+                hm.perm[(size_t)(k0 + cnt[(size_t)(key(c) - key0)]++)] = c;
+            }
+        }
+    }
+    hm.rowptr[(size_t)I] = (int32_t)nnz;
+    return true;
+}
+
+bool cut_segments(HostMode& hm, int items) {
+    const int64_t I = hm.I, nnz = hm.nnz, total = I + nnz;
+    const int64_t S = (total + items - 1) / items;
+    hm.S = (int32_t)S;
+    if (!hm.seg_row.alloc((size_t)S + 1) || !hm.seg_nz.alloc((size_t)S + 1)) return false;
+    const int32_t* rp = hm.rowptr.p;
+    // Boundary d = s*items on the merge path: the end of row i sits at position
+    // rowptr[i+1] + i; the rows completed before d are those whose end lies
+    // before d, found by binary search; the rest of d counts consumed nonzeros.
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s <= S; ++s) {
+        const int64_t d = std::min(total, s * (int64_t)items);
+        int64_t lo = 0, hi = I;  // first row whose end position is >= d
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if ((int64_t)rp[mid + 1] + mid < d) lo = mid + 1; else hi = mid;
+        }
+        hm.seg_row[(size_t)s] = (int32_t)lo;
+        hm.seg_nz[(size_t)s] = (int32_t)(d - lo);
+    }
+    // split rows: boundary s is straddled when its row started before it
+    std::vector<SplitRow> sp;
+    for (int64_t s = 1; s < S; ++s) {
+        const int32_t r = hm.seg_row[(size_t)s];
+        if (r >= I || hm.seg_nz[(size_t)s] <= rp[r]) continue;
+        if (!sp.empty() && sp.back().row == r && sp.back().s_b == s - 1)
+            sp.back().s_b = (int32_t)s;
+        else
+            sp.push_back({r, (int32_t)s, (int32_t)s});
+    }
+    hm.nsplit = (int32_t)sp.size();
+    if (!hm.splits.alloc(sp.size())) return false;
+    if (!sp.empty()) std::memcpy(hm.splits.p, sp.data(), sp.size() * sizeof(SplitRow));
+    // combine tasks: the slots of split row j are T[s_a-1], H[s_a], ..., H[s_b],
+    // cut into runs of at most kCombineSlots consecutive segments
+    std::vector<int32_t> tasks, info, multi;
+    for (int32_t j = 0; j < hm.nsplit; ++j) {
+        const SplitRow& r = sp[(size_t)j];
+        info.push_back(r.row);
+        info.push_back((int32_t)(tasks.size() / 4));
+        int32_t nt = 0;
+        for (int32_t lo = r.s_a - 1; lo <= r.s_b; lo += kCombineSlots, ++nt) {
+            tasks.push_back(j);
+            tasks.push_back(lo);
+            tasks.push_back(std::min(lo + kCombineSlots, r.s_b + 1));
+            tasks.push_back(lo == r.s_a - 1 ? 1 : 0);
+        }
+        if (nt > 1) multi.push_back(j);
+    }
+    info.push_back(0);
+    info.push_back((int32_t)(tasks.size() / 4));
+    hm.ntask = (int32_t)(tasks.size() / 4);
+    hm.nmulti = (int32_t)multi.size();
+    if (!hm.tasks.alloc(tasks.size()) || !hm.split_info.alloc(info.size()) || !hm.multi.alloc(multi.size()))
+        return false;
+    if (!tasks.empty()) std::memcpy(hm.tasks.p, tasks.data(), tasks.size() * 4);
+    std::memcpy(hm.split_info.p, info.data(), info.size() * 4);
+    if (!multi.empty()) std::memcpy(hm.multi.p, multi.data(), multi.size() * 4);
+    return true;
+}
+
+void gather_column(const HostMode& hm, int nmodes, const int32_t* idx, int src_mode, int32_t* dst, int threads) {
+    const int T = nthreads(threads);
+#pragma omp parallel for schedule(static) num_threads(T)
+    for (int64_t k = 0; k < hm.nnz; ++k) dst[k] = idx[(int64_t)hm.perm[(size_t)k] * nmodes + src_mode];
+}
+
+void gather_values(const HostMode& hm, const float* vals, float* dst, int threads) {
+    const int T = nthreads(threads);
+#pragma omp parallel for schedule(static) num_threads(T)
+    for (int64_t k = 0; k < hm.nnz; ++k) dst[k] = vals[hm.perm[(size_t)k]];
+}
+
+void caller_column(int64_t nnz, int nmodes, const int32_t* idx, int mode, int32_t* dst, int threads) {
+    const int T = nthreads(threads);
+#pragma omp parallel for schedule(static) num_threads(T)
+    for (int64_t k = 0; k < nnz; ++k) dst[k] = idx[k * nmodes + mode];
+}
+
+}  // namespace amped

@@ -1,0 +1,201 @@
+"""Python face of the library: a sparse tensor handle with MTTKRP, the
+sampled CP model and its gradient.  PyTorch provides device memory and
+streams only; the work is done by the CUDA library behind the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import _lib
+
+try:
+    import torch
+except ImportError:  # the planning query works without torch
+    torch = None
+
+
+def _dtype_code(t) -> int:
+    if t.dtype == torch.float32:
+        return _lib.F32
+    if t.dtype == torch.bfloat16:
+        return _lib.BF16
+    if t.dtype == torch.float16:
+        return _lib.F16
+    raise TypeError(f"factor dtype {t.dtype} is not one of float32, bfloat16, float16")
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Tensor:
+    """An N-mode sparse COO tensor resident on the current CUDA device.
+
+    ``idx`` is int32 [nnz, N] (0-based), ``vals`` float32 [nnz]; both host
+    arrays (numpy or CPU torch).  Construction builds one output-row-ordered,
+    segmented copy per mode on the device (paper Sec. 3); it is synchronous.
+    """
+
+    def __init__(self, dims, idx, vals, *, segment_items: int = 0, keep_perm: bool = True, keep_coo: bool = True,
+                 max_rank: int = 0, host_threads: int = 0):
+        L = _lib.lib()
+        self.dims = tuple(int(d) for d in dims)
+        idx = np.ascontiguousarray(idx.numpy() if hasattr(idx, "numpy") else idx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals.numpy() if hasattr(vals, "numpy") else vals, dtype=np.float32)
+        if idx.ndim != 2 or idx.shape[1] != len(self.dims) or vals.shape != (idx.shape[0],):
+            raise ValueError("idx must be [nnz, N] and vals [nnz]")
+        self.nnz = int(idx.shape[0])
+        dims_a = np.asarray(self.dims, dtype=np.int64)
+        opts = _lib.Opts(segment_items, 1 if keep_perm else 2, 1 if keep_coo else 2, max_rank, host_threads)
+        h = ctypes.c_void_p()
+        _lib.check(L.amped_tensor_create(self.nnz, len(self.dims), dims_a.ctypes.data,
+                                         idx.ctypes.data if self.nnz else None,
+                                         vals.ctypes.data if self.nnz else None, ctypes.byref(opts),
+                                         ctypes.byref(h)))
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device()) if torch is not None else None
+
+    # ------------------------------------------------------------------ lifetime
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.lib().amped_tensor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def nmodes(self) -> int:
+        return len(self.dims)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise ValueError("tensor handle is closed")
+        return self._h
+
+    # ------------------------------------------------------------------ helpers
+    def _factors(self, factors, skip=-1):
+        if len(factors) != self.nmodes:
+            raise ValueError(f"need {self.nmodes} factors")
+        ref = next(f for n, f in enumerate(factors) if n != skip and f is not None)
+        R = int(ref.shape[1])
+        code = _dtype_code(ref)
+        ptrs = []
+        for n, f in enumerate(factors):
+            if n == skip and f is None:
+                ptrs.append(None)
+                continue
+            if f.dtype != ref.dtype or not f.is_cuda or not f.is_contiguous() or tuple(f.shape) != (self.dims[n], R):
+                raise ValueError(f"factor {n} must be a contiguous CUDA [{self.dims[n]}, {R}] {ref.dtype} tensor")
+            ptrs.append(f.data_ptr())
+        return _lib.ptr_array(ptrs), code, R
+
+    def _out(self, n, R, out):
+        if out is None:
+            return torch.empty((self.dims[n], R), dtype=torch.float32, device=self.device)
+        if out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != (self.dims[n], R):
+            raise ValueError(f"output {n} must be a contiguous float32 [{self.dims[n]}, {R}] tensor")
+        return out
+
+    # ------------------------------------------------------------------ operations
+    def mttkrp(self, mode: int, factors, out=None, stream=None):
+        """Mode-`mode` MTTKRP: out[i] = sum over nonzeros with i_mode = i of
+        val * Hadamard product of the other factors' rows (fp32 result)."""
+        fp, code, R = self._factors(factors, skip=mode)
+        out = self._out(mode, R, out)
+        _lib.check(_lib.lib().amped_mttkrp(self.handle, mode, fp, code, R, out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def mttkrp_all(self, factors, outs=None, stream=None):
+        """MTTKRP for every mode with the same input factors."""
+        fp, code, R = self._factors(factors)
+        outs = [self._out(n, R, None if outs is None else outs[n]) for n in range(self.nmodes)]
+        op = _lib.ptr_array([o.data_ptr() for o in outs])
+        _lib.check(_lib.lib().amped_mttkrp_all(self.handle, fp, code, R, op, _stream_ptr(stream)))
+        return outs
+
+    def mttkrp_all_host(self, factors, outs=None, stream=None):
+        """All-mode MTTKRP on host (CPU) tensors: the library copies the factors
+        in, runs every mode and copies the outputs back before returning."""
+        if len(factors) != self.nmodes:
+            raise ValueError(f"need {self.nmodes} factors")
+        R = int(factors[0].shape[1])
+        code = _dtype_code(factors[0])
+        for n, f in enumerate(factors):
+            if f.is_cuda or not f.is_contiguous() or tuple(f.shape) != (self.dims[n], R) or f.dtype != factors[0].dtype:
+                raise ValueError(f"host factor {n} must be a contiguous CPU [{self.dims[n]}, {R}] tensor")
+        if outs is None:
+            outs = [torch.empty((d, R), dtype=torch.float32) for d in self.dims]
+        for n, o in enumerate(outs):
+            if o.is_cuda or o.dtype != torch.float32 or not o.is_contiguous() or tuple(o.shape) != (self.dims[n], R):
+                raise ValueError(f"host output {n} must be a contiguous CPU float32 [{self.dims[n]}, {R}] tensor")
+        fp = _lib.ptr_array([f.data_ptr() for f in factors])
+        op = _lib.ptr_array([o.data_ptr() for o in outs])
+        _lib.check(_lib.lib().amped_mttkrp_all_host(self.handle, fp, code, R, op, _stream_ptr(stream)))
+        return outs
+
+    def cp_sample(self, factors, out=None, stream=None):
+        """Sampled CP model m[k] = sum_r prod_n A_n(i_n(k), r), caller order."""
+        fp, code, R = self._factors(factors)
+        if out is None:
+            out = torch.empty(self.nnz, dtype=torch.float32, device=self.device)
+        _lib.check(_lib.lib().amped_cp_sample(self.handle, fp, code, R, out.data_ptr() if self.nnz else None,
+                                              _stream_ptr(stream)))
+        return out
+
+    def cp_grad(self, factors, gvals, grads=None, stream=None):
+        """d L / d A_n for every n given gvals[k] = dL/dm_k (caller order)."""
+        fp, code, R = self._factors(factors)
+        if gvals.dtype != torch.float32 or not gvals.is_cuda or gvals.numel() != self.nnz:
+            raise ValueError("gvals must be a float32 CUDA tensor with one entry per nonzero")
+        gvals = gvals.contiguous()
+        grads = [self._out(n, R, None if grads is None else grads[n]) for n in range(self.nmodes)]
+        gp = _lib.ptr_array([g.data_ptr() for g in grads])
+        _lib.check(_lib.lib().amped_cp_grad(self.handle, fp, code, R, gvals.data_ptr() if self.nnz else None, gp,
+                                            _stream_ptr(stream)))
+        return grads
+
+    def set_kernel_events(self, start, stop) -> None:
+        """Record torch.cuda.Event `start`/`stop` around the next MTTKRP kernel."""
+        for ev in (start, stop):
+            if ev is not None and not ev.cuda_event:
+                ev.record()  # events are created lazily by torch
+        _lib.check(_lib.lib().amped_set_kernel_events(self.handle, start.cuda_event if start else None,
+                                                      stop.cuda_event if stop else None))
+
+
+def plan_mode(dims, idx, mode: int, segment_items: int = 0) -> dict:
+    """Host-only: the reorder and merge-path segment table for one mode."""
+    L = _lib.lib()
+    dims_a = np.asarray(dims, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    nnz = int(idx.shape[0])
+    I = int(dims_a[mode])
+    items = segment_items if segment_items > 0 else 1024
+    S = -(-(I + nnz) // items)
+    perm = np.empty(nnz, np.int32)
+    rowptr = np.empty(I + 1, np.int32)
+    seg_row = np.empty(S + 1, np.int32)
+    seg_nz = np.empty(S + 1, np.int32)
+    splits = np.empty((max(S, 1), 3), np.int32)
+    ns = ctypes.c_int32()
+    _lib.check(L.amped_plan_mode(nnz, len(dims_a), dims_a.ctypes.data, idx.ctypes.data if nnz else None, mode,
+                                 segment_items, perm.ctypes.data, rowptr.ctypes.data, seg_row.ctypes.data,
+                                 seg_nz.ctypes.data, splits.ctypes.data, ctypes.byref(ns)))
+    return {"perm": perm, "rowptr": rowptr, "seg_row": seg_row, "seg_nz": seg_nz, "splits": splits[: ns.value],
+            "items": items, "S": S}

@@ -1,0 +1,290 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Bars: fp32 factors -> max relative row error <= 1e-5; bf16/fp16 factors ->
+<= 1e-5 against the oracle run on the same rounded factors (kernel
+arithmetic) and <= 2e-2 against the oracle on the original fp32 factors
+(storage rounding included); gradients (mixed-sign values) -> <= 1e-4 with
+the denominator floored at 1e-6 of the largest row.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2507_15121_gb300 as amped  # noqa: E402
+
+FP32_BAR = 1e-5
+LOWP_BAR = 2e-2
+GRAD_BAR = 1e-4
+
+
+def dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host_bits(t):
+    """raw uint16 bit patterns of a bf16/fp16 CUDA tensor (oracle input)."""
+    return t.detach().cpu().view(torch.int16).numpy().view(np.uint16)
+
+
+def run_all(c, F, dtype=torch.float32, items=0, R=None):
+    t = amped.Tensor(c.dims, c.idx, c.vals, segment_items=items)
+    Fd = [dev(f, dtype) for f in F]
+    outs = t.mttkrp_all(Fd)
+    torch.cuda.synchronize()
+    res = [o.cpu().numpy() for o in outs]
+    t.close()
+    return res, Fd
+
+
+def check_fp32(c, F, items=0, bar=FP32_BAR):
+    got, _ = run_all(c, F, items=items)
+    for m in range(c.nmodes):
+        ref = oracle.mttkrp(c.dims, c.idx, c.vals, F, m)
+        err = oracle.row_error(got[m], ref)
+        assert err <= bar, (m, err)
+
+
+# --------------------------------------------------------------------------- configs at test size
+def test_uniform3_full_size_fp32():
+    """3-mode 1000x800x600, 100k uniform nonzeros (duplicates merged), R=16."""
+    w = synth.WORKLOADS["uniform3"]
+    c = synth.make(w)
+    F = synth.factors(c.dims, w.rank, w.seed)
+    check_fp32(c, F)
+
+
+@pytest.mark.parametrize("scale", [0.001, 0.005])
+def test_zipf3_reduced_fp32(scale):
+    w = synth.WORKLOADS["zipf3"].scaled(scale)
+    c = synth.make(w)
+    F = synth.factors(c.dims, 32, w.seed)
+    check_fp32(c, F)
+
+
+def test_zipf4_reduced_fp32():
+    w = synth.WORKLOADS["zipf4"].scaled(0.0003)
+    c = synth.make(w)
+    F = synth.factors(c.dims, 32, w.seed)
+    check_fp32(c, F)
+
+
+@pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("R", [32, 64])
+def test_zipf3_16bit_factors(dt, R):
+    w = synth.WORKLOADS["zipf3_r64"].scaled(0.001)
+    c = synth.make(w)
+    F = synth.factors(c.dims, R, w.seed)
+    got, Fd = run_all(c, F, dtype=dt)
+    name = "bf16" if dt == torch.bfloat16 else "f16"
+    bits = [host_bits(f) for f in Fd]
+    for m in range(3):
+        ref_rounded = oracle.mttkrp(c.dims, c.idx, c.vals, bits, m, name)
+        ref_fp32 = oracle.mttkrp(c.dims, c.idx, c.vals, F, m)
+        assert oracle.row_error(got[m], ref_rounded) <= FP32_BAR
+        assert oracle.row_error(got[m], ref_fp32) <= LOWP_BAR
+
+
+# --------------------------------------------------------------------------- shapes and edge cases
+@pytest.mark.parametrize("items", [1, 7, 32, 1024, 10 ** 7])
+def test_segment_length_sweep(items):
+    rng = np.random.default_rng(items)
+    dims = (300, 200, 100)
+    nnz = 20000
+    idx = np.stack([rng.integers(0, d, nnz) for d in dims], axis=1).astype(np.int32)
+    idx[:5000, 0] = 17  # one long row in mode 0
+    c = synth.Coo(dims, idx, rng.uniform(0, 1, nnz).astype(np.float32))
+    F = [rng.uniform(0, 1, (d, 32)).astype(np.float32) for d in dims]
+    check_fp32(c, F, items=items)
+
+
+@pytest.mark.parametrize("R", [1, 3, 8, 16, 24, 32, 48, 64, 128])
+def test_rank_sweep_fp32(R):
+    rng = np.random.default_rng(R)
+    dims = (500, 300, 200)
+    nnz = 30000
+    idx = np.stack([rng.integers(0, d, nnz) for d in dims], axis=1).astype(np.int32)
+    c = synth.Coo(dims, idx, rng.uniform(0, 1, nnz).astype(np.float32))
+    F = [rng.uniform(0, 1, (d, R)).astype(np.float32) for d in dims]
+    check_fp32(c, F, items=512)
+
+
+@pytest.mark.parametrize("R", [5, 8, 16, 32, 128, 256])
+def test_rank_sweep_bf16(R):
+    rng = np.random.default_rng(100 + R)
+    dims = (400, 300, 200)
+    nnz = 20000
+    idx = np.stack([rng.integers(0, d, nnz) for d in dims], axis=1).astype(np.int32)
+    c = synth.Coo(dims, idx, rng.uniform(0, 1, nnz).astype(np.float32))
+    F = [rng.uniform(0, 1, (d, R)).astype(np.float32) for d in dims]
+    got, Fd = run_all(c, F, dtype=torch.bfloat16)
+    bits = [host_bits(f) for f in Fd]
+    for m in range(3):
+        assert oracle.row_error(got[m], oracle.mttkrp(c.dims, c.idx, c.vals, bits, m, "bf16")) <= FP32_BAR
+
+
+def test_unsupported_rank_is_an_error():
+    c = synth.Coo((4, 4, 4), np.zeros((1, 3), np.int32), np.ones(1, np.float32))
+    t = amped.Tensor(c.dims, c.idx, c.vals)
+    F = [torch.ones((4, 130), device="cuda") for _ in range(3)]  # fp32 R=130: no kernel
+    with pytest.raises(amped.AmpedError) as e:
+        t.mttkrp(0, F)
+    assert e.value.status == -5
+
+
+def test_edge_cases():
+    rng = np.random.default_rng(5)
+    R = 32
+    # empty tensor: every output row is exactly zero
+    c = synth.Coo((7, 5, 3), np.zeros((0, 3), np.int32), np.zeros(0, np.float32))
+    got, _ = run_all(c, [np.ones((d, R), np.float32) for d in c.dims])
+    assert all(np.all(g == 0) for g in got)
+    # single nonzero
+    c = synth.Coo((7, 5, 3), np.array([[6, 0, 2]], np.int32), np.array([2.5], np.float32))
+    check_fp32(c, [rng.uniform(0, 1, (d, R)).astype(np.float32) for d in c.dims])
+    # one row holds every nonzero; a mode of size 1
+    nnz = 50000
+    idx = np.stack([np.full(nnz, 3), rng.integers(0, 1, nnz), rng.integers(0, 900, nnz)], 1).astype(np.int32)
+    c = synth.Coo((10, 1, 900), idx, rng.uniform(0, 1, nnz).astype(np.float32))
+    check_fp32(c, [rng.uniform(0, 1, (d, R)).astype(np.float32) for d in c.dims], items=256)
+    # two modes (sparse matrix times dense)
+    dims = (700, 500)
+    idx = np.stack([rng.integers(0, d, 9000) for d in dims], 1).astype(np.int32)
+    c = synth.Coo(dims, idx, rng.uniform(0, 1, 9000).astype(np.float32))
+    check_fp32(c, [rng.uniform(0, 1, (d, R)).astype(np.float32) for d in dims])
+    # hyper-sparse: 40 nonzeros over a million rows
+    dims = (1_000_000, 20, 30)
+    idx = np.stack([rng.integers(0, d, 40) for d in dims], 1).astype(np.int32)
+    c = synth.Coo(dims, idx, rng.uniform(0, 1, 40).astype(np.float32))
+    check_fp32(c, [rng.uniform(0, 1, (d, R)).astype(np.float32) for d in dims])
+
+
+def test_repeat_calls_and_single_mode_entry():
+    w = synth.WORKLOADS["zipf3"].scaled(0.0005)
+    c = synth.make(w)
+    F = synth.factors(c.dims, 32, w.seed)
+    t = amped.Tensor(c.dims, c.idx, c.vals)
+    Fd = [dev(f) for f in F]
+    a = [t.mttkrp(m, Fd).cpu().numpy() for m in range(3)]
+    b = [o.cpu().numpy() for o in t.mttkrp_all(Fd)]
+    for m in range(3):  # the split-row combine is deterministic: identical results
+        np.testing.assert_array_equal(a[m], b[m])
+    host = t.mttkrp_all_host([torch.from_numpy(f) for f in F])
+    for m in range(3):
+        np.testing.assert_array_equal(host[m].numpy(), b[m])
+    assert amped.kernel_launches() > 0
+
+
+# --------------------------------------------------------------------------- sampled model and gradient
+def test_cp_sample_and_grad_against_oracle():
+    w = synth.WORKLOADS["planted3"].scaled(0.0005)
+    c = synth.make(w)
+    # planted values: the oracle evaluates the planted CP model, plus the noise
+    x = (oracle.cp_sample(c.dims, c.idx, c.extra["planted_factors"]) + c.extra["noise"]).astype(np.float32)
+    F = synth.factors(c.dims, 32, w.seed, scale=w.factor_scale)
+    t = amped.Tensor(c.dims, c.idx, x)
+    Fd = [dev(f) for f in F]
+    m = t.cp_sample(Fd).cpu().numpy()
+    m_ref = oracle.cp_sample(c.dims, c.idx, F)
+    assert np.max(np.abs(m - m_ref) / np.abs(m_ref)) <= FP32_BAR
+    g = (m_ref - x.astype(np.float64))
+    grads = t.cp_grad(Fd, dev(g.astype(np.float32)))
+    ref = oracle.cp_grad(c.dims, c.idx, g.astype(np.float32).astype(np.float64), F)
+    for n in range(3):
+        assert oracle.row_error(grads[n].cpu().numpy(), ref[n], floor_frac=1e-6) <= GRAD_BAR
+
+
+def test_autograd_completion_step_gradient_check():
+    """Planted rank-16 CP tensor; on a 1k-nonzero subset the autograd gradient
+    of L = 1/2 sum (m - x)^2 matches the FP64 oracle gradient and FP64
+    central finite differences of the oracle loss."""
+    w = synth.WORKLOADS["planted3"].scaled(0.0002)
+    c = synth.make(w)
+    sub = synth.subset(c.nnz, 1000, w.seed)
+    idx = np.ascontiguousarray(c.idx[sub])
+    x = (oracle.cp_sample(c.dims, idx, c.extra["planted_factors"]) + c.extra["noise"][sub]).astype(np.float32)
+    F = synth.factors(c.dims, 32, w.seed, scale=w.factor_scale)
+    t = amped.Tensor(c.dims, idx, x)
+    Fd = [dev(f).requires_grad_(True) for f in F]
+    loss = amped.completion_loss(t, Fd, dev(x))
+    loss.backward()
+    L_ref, G_ref = oracle.completion_grad(c.dims, idx, x, F)
+    assert abs(loss.item() - L_ref) <= 1e-5 * L_ref
+    for n in range(3):
+        assert oracle.row_error(Fd[n].grad.cpu().numpy(), G_ref[n], floor_frac=1e-6) <= GRAD_BAR
+    # finite differences of the FP64 oracle loss on entries touched by the subset
+    rng = np.random.default_rng(0)
+    F64 = [f.astype(np.float64) for f in F]
+    for n in range(3):
+        rows = np.unique(idx[:, n])
+        for _ in range(4):
+            i, r = int(rng.choice(rows)), int(rng.integers(0, 32))
+            h = 1e-6 * max(1.0, abs(F64[n][i, r]))
+            Fp = [f.copy() for f in F64]
+            Fm = [f.copy() for f in F64]
+            Fp[n][i, r] += h
+            Fm[n][i, r] -= h
+            lp = oracle.completion_loss(oracle_cp_sample64(c.dims, idx, Fp), x)
+            lm = oracle.completion_loss(oracle_cp_sample64(c.dims, idx, Fm), x)
+            fd = (lp - lm) / (2 * h)
+            gpu = float(Fd[n].grad[i, r])
+            assert abs(gpu - fd) <= 1e-4 * max(1.0, abs(fd)), (n, i, r, gpu, fd)
+
+
+def oracle_cp_sample64(dims, idx, F64):
+    """The sampled model for fp64 factors: the oracle's fp32 interface would
+    round the perturbed factors, so evaluate the definition with numpy here."""
+    p = np.ones((idx.shape[0], F64[0].shape[1]))
+    for n in range(len(dims)):
+        p *= F64[n][idx[:, n]]
+    return p.sum(axis=1)
+
+
+def test_planted_model_residual_is_noise():
+    """With the planted factors as the model, the residual is the added noise."""
+    w = synth.WORKLOADS["planted3"].scaled(0.0002)
+    c = synth.make(w)
+    B = c.extra["planted_factors"]
+    x = (oracle.cp_sample(c.dims, c.idx, B) + c.extra["noise"]).astype(np.float32)
+    t = amped.Tensor(c.dims, c.idx, x)
+    m = t.cp_sample([dev(b) for b in B]).cpu().numpy()
+    resid = m - x
+    assert abs(resid.std() - w.noise_sd) < 0.1 * w.noise_sd
+
+
+# --------------------------------------------------------------------------- full size, sampled rows
+def sampled_rows(c, mode, k, seed):
+    counts = np.bincount(c.idx[:, mode], minlength=c.dims[mode])
+    hot = np.argsort(-counts, kind="stable")[:16]
+    rows = np.unique(np.concatenate([hot, synth.subset(c.dims[mode], k, seed + mode)]))
+    return rows
+
+
+@pytest.mark.slow
+def test_zipf3_full_size_sampled_rows():
+    """10M x 5M x 2M, 200M Zipf(1.1) nonzeros, R=32, fp32 and bf16 factors, in the
+    launch configuration the benchmark times; the oracle recomputes 4096 seeded
+    rows per mode (plus the 16 hottest) in one pass over the COO."""
+    w = synth.WORKLOADS["zipf3"]
+    c = synth.make(w)
+    F = synth.factors(c.dims, 32, w.seed)
+    t = amped.Tensor(c.dims, c.idx, c.vals)
+    Fd = [dev(f) for f in F]
+    outs = [o.cpu().numpy() for o in t.mttkrp_all(Fd)]
+    Fb = [f.to(torch.bfloat16) for f in Fd]
+    outs_b = [o.cpu().numpy() for o in t.mttkrp_all(Fb)]
+    del Fd, Fb
+    t.close()
+    for m in range(3):
+        rows = sampled_rows(c, m, 4096, w.seed)
+        ref = oracle.mttkrp_rows(c.dims, c.idx, c.vals, F, m, rows)
+        assert oracle.row_error(outs[m][rows], ref) <= FP32_BAR, m
+        assert oracle.row_error(outs_b[m][rows], ref) <= LOWP_BAR, m
+        # rows that no nonzero touches are exactly zero
+        counts = np.bincount(c.idx[:, m], minlength=c.dims[m])
+        empty = np.flatnonzero(counts == 0)[:1000]
+        assert np.all(outs[m][empty] == 0)

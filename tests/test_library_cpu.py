@@ -1,0 +1,192 @@
+"""CPU-side checks of the CUDA library: it loads, exports every symbol the
+header declares, rejects bad arguments before touching the GPU, and its host
+reorder / merge-path segment plan satisfies the invariants the kernel relies
+on.  A Python walk of the plan with the kernel's flush rules (complete rows
+stored, head/tail partials of split rows combined in order) reproduces the
+FP64 oracle, which checks the split-row bookkeeping without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2507_15121_gb300 import _lib, plan_mode
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "amped.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2507_15121_gb300 import build
+    build.build()
+    return _lib.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(amped_\w+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert "amped_mttkrp" in names and "amped_tensor_create" in names and "amped_cp_grad" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert L.amped_version().decode().startswith("amped-gb300")
+
+
+def _create(L, nnz, dims, idx, vals):
+    dims_a = np.asarray(dims, dtype=np.int64)
+    h = ctypes.c_void_p()
+    rc = L.amped_tensor_create(nnz, len(dims), dims_a.ctypes.data if len(dims) else None,
+                               None if idx is None else idx.ctypes.data, None if vals is None else vals.ctypes.data,
+                               None, ctypes.byref(h))
+    return rc, h
+
+
+def test_argument_errors_without_gpu(L):
+    idx = np.array([[0, 1], [2, 0]], dtype=np.int32)
+    vals = np.ones(2, np.float32)
+    assert _create(L, 2, (), idx, vals)[0] == _lib.ERR_INVALID
+    assert _create(L, -1, (3, 2), idx, vals)[0] == _lib.ERR_INVALID
+    assert _create(L, 2, (0, 2), idx, vals)[0] == _lib.ERR_INVALID
+    assert _create(L, 2, (3, 2), None, vals)[0] == _lib.ERR_INVALID
+    assert _create(L, 2, tuple([2] * 9), np.zeros((2, 9), np.int32), vals)[0] == _lib.ERR_INVALID
+    bad = np.array([[0, 1], [3, 0]], dtype=np.int32)  # 3 is outside dims[0] = 3
+    rc, h = _create(L, 2, (3, 2), bad, vals)
+    assert rc == _lib.ERR_INDEX and not h.value
+    assert b"nonzero 1" in L.amped_last_error()
+    neg = np.array([[0, -1]], dtype=np.int32)
+    assert _create(L, 1, (3, 2), neg, vals[:1])[0] == _lib.ERR_INDEX
+    # calls on a NULL handle fail cleanly
+    assert L.amped_mttkrp(None, 0, None, 0, 32, None, None) == _lib.ERR_INVALID
+    assert L.amped_tensor_destroy(None) == _lib.OK
+
+
+def check_plan(dims, idx, mode, items):
+    p = plan_mode(dims, idx, mode, items)
+    nnz, I = idx.shape[0], dims[mode]
+    keys = idx[:, mode]
+    # stable order by the mode's coordinate
+    np.testing.assert_array_equal(p["perm"], np.argsort(keys, kind="stable"))
+    np.testing.assert_array_equal(p["rowptr"], np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=I))]))
+    sr, sz, S = p["seg_row"].astype(np.int64), p["seg_nz"].astype(np.int64), p["S"]
+    total = I + nnz
+    d = np.minimum(np.arange(S + 1, dtype=np.int64) * p["items"], total)
+    np.testing.assert_array_equal(sr + sz, d)
+    assert sr[0] == 0 and sz[0] == 0 and sr[-1] == I and sz[-1] == nnz
+    assert np.all(np.diff(sr) >= 0) and np.all(np.diff(sz) >= 0)
+    rp = p["rowptr"].astype(np.int64)
+    # merge-path consistency: rows before seg_row are complete, the current row is partly consumed
+    for s in range(S + 1):
+        r = sr[s]
+        if r < I:
+            assert rp[r] <= sz[s] <= rp[r + 1]
+        if r > 0:
+            assert rp[r] <= sz[s]
+    # split rows = rows straddling boundaries, grouped by row
+    straddled = [(int(sr[s]), s) for s in range(1, S) if sr[s] < I and sz[s] > rp[sr[s]]]
+    exp = []
+    for r, s in straddled:
+        if exp and exp[-1][0] == r and exp[-1][2] == s - 1:
+            exp[-1][2] = s
+        else:
+            exp.append([r, s, s])
+    np.testing.assert_array_equal(p["splits"].reshape(-1, 3), np.array(exp, dtype=np.int32).reshape(-1, 3))
+    return p
+
+
+def simulate_kernel(p, dims, idx, vals, F, mode):
+    """The MTTKRP kernel's per-segment walk and flush rules, then the
+    deterministic combine of split rows, in plain Python (fp64)."""
+    I = dims[mode]
+    R = F[0].shape[1]
+    perm, rp = p["perm"], p["rowptr"].astype(np.int64)
+    contrib = vals[perm].astype(np.float64)[:, None] * np.ones((1, R))
+    for n in range(len(dims)):
+        if n != mode:
+            contrib = contrib * F[n][idx[perm, n]].astype(np.float64)
+    out = np.full((I, R), np.nan)
+    H, T = {}, {}
+    sr, sz = p["seg_row"], p["seg_nz"]
+    for s in range(p["S"]):
+        row_s, nz_s, row_e, nz_e = int(sr[s]), int(sz[s]), int(sr[s + 1]), int(sz[s + 1])
+        cont = rp[row_s] < nz_s
+        st = {"i": row_s, "acc": np.zeros(R), "touched": False}
+
+        def rend():
+            return rp[st["i"] + 1] if st["i"] < row_e else nz_e
+
+        def flush(row):
+            if row == row_s and cont:
+                assert s not in H
+                H[s] = st["acc"].copy()
+            elif row < row_e:
+                assert np.isnan(out[row, 0]), "row written twice"
+                out[row] = st["acc"]
+            else:
+                assert s not in T
+                T[s] = st["acc"].copy()
+            st["acc"][:] = 0
+            st["touched"] = False
+
+        for k in range(nz_s, nz_e):
+            while k >= rend():
+                flush(st["i"])
+                st["i"] += 1
+            st["acc"] += contrib[k]
+            st["touched"] = True
+        while st["i"] < row_e:
+            flush(st["i"])
+            st["i"] += 1
+        if st["i"] < I and st["touched"]:
+            flush(st["i"])
+    for row, s_a, s_b in p["splits"]:
+        assert np.isnan(out[row, 0])
+        out[row] = T[s_a - 1] + sum(H[s] for s in range(s_a, s_b + 1))
+    assert not np.any(np.isnan(out)), "a row was never written"
+    return out
+
+
+CASES = [
+    ("uniform-small", (30, 20, 10), 400, 1),
+    ("one-long-row", (50, 6, 5), 300, 2),
+    ("hypersparse", (5000, 7, 3), 40, 3),
+    ("four-modes", (12, 9, 8, 5), 500, 4),
+    ("two-modes", (40, 30), 250, 5),
+]
+
+
+def make_case(name, dims, nnz, seed):
+    rng = np.random.default_rng(seed)
+    idx = np.stack([rng.integers(0, d, nnz) for d in dims], axis=1).astype(np.int32)
+    if name == "one-long-row":
+        idx[: nnz * 2 // 3, 0] = 7  # most nonzeros in one output row of mode 0
+    vals = rng.uniform(0, 1, nnz).astype(np.float32)
+    return idx, vals
+
+
+@pytest.mark.parametrize("name,dims,nnz,seed", CASES)
+@pytest.mark.parametrize("items", [1, 7, 32, 1024, 10 ** 6])
+def test_plan_and_simulated_kernel_match_oracle(name, dims, nnz, seed, items):
+    idx, vals = make_case(name, dims, nnz, seed)
+    F = [np.random.default_rng(seed + n).uniform(0, 1, (d, 3)).astype(np.float32) for n, d in enumerate(dims)]
+    for mode in range(len(dims)):
+        p = check_plan(dims, idx, mode, items)
+        got = simulate_kernel(p, dims, idx, vals, F, mode)
+        np.testing.assert_allclose(got, oracle.mttkrp(dims, idx, vals, F, mode), rtol=1e-12, atol=1e-12)
+
+
+def test_plan_empty_tensor_and_zipf():
+    dims = (10, 4, 3)
+    p = check_plan(dims, np.zeros((0, 3), np.int32), 0, 4)
+    assert p["S"] == 3 and len(p["splits"]) == 0
+    w = synth.WORKLOADS["zipf3"].scaled(0.0002)
+    c = synth.make(w)
+    for mode in range(3):
+        check_plan(c.dims, c.idx, mode, 256)
