@@ -327,7 +327,7 @@ def run_ours(args, w, world, rank, local, pg):
             t.mttkrp_all_host(Fh, Oh)
         e2e_s = max_over_ranks(time.perf_counter() - t1, pg, device)
         line["e2e"] = {"value": world * c.nnz * Ke / e2e_s / 1e9, "unit": UNIT, "steps": Ke,
-                       "h2d_bytes_per_step": int(sum(f.numel() * 4 for f in F)),
+                       "h2d_bytes_per_step": int(sum(f.size * 4 for f in F)),
                        "d2h_bytes_per_step": int(sum(o.numel() * 4 for o in Oh)),
                        "entry": "amped_mttkrp_all_host (pinned host factors and outputs)"}
         del Fh, Oh
