@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--workload", default="zipf3", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--scale", type=float, default=1.0, help="scale nnz and dims (debug)")
     ap.add_argument("--segment-items", type=int, default=0)
+    ap.add_argument("--inner-order", default="lexicographic", choices=["lexicographic", "stable"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
@@ -95,51 +96,49 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    """Polls nvidia-smi (one query every ~100 ms, in a thread) for the SM clock
+    and throttle reasons while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
-        self.proc = None
+        self.rows = []
+        self.result = None
+        self._stop = None
+
+    def _poll(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout
+                f = [x.strip() for x in out.strip().split(",")]
+                if len(f) >= 7:
+                    self.rows.append((float(f[0]), float(f[1]), f[2], f[3:7]))
+            except Exception:
+                pass
+            self._stop.wait(0.1)
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except Exception:
-            self.proc = None
-        time.sleep(0.3)
+        import threading
+        self._stop = threading.Event()
+        self._thr = threading.Thread(target=self._poll, daemon=True)
+        self._thr.start()
         return self
 
     def __exit__(self, *a):
-        time.sleep(0.15)
-        self.result = None
-        if self.proc is None:
+        self._stop.set()
+        self._thr.join(timeout=10)
+        if not self.rows:
             return
-        self.proc.terminate()
-        try:
-            out, _ = self.proc.communicate(timeout=5)
-        except Exception:
-            self.proc.kill()
-            out = ""
-        rows = []
-        for line in out.strip().splitlines():
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                rows.append((float(f[0]), float(f[1]), f[4:9]))
-            except ValueError:
-                pass
-        if not rows:
-            return
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl[1:]) if v.lower() == "active"})
-        self.result = {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                       "samples": len(rows), "reasons": reasons}
+        reasons = sorted({self.NAMES[i] for *_, fl in self.rows for i, v in enumerate(fl)
+                          if v.lower() == "active"})
+        self.result = {"sm_mhz": statistics.median(r[0] for r in self.rows),
+                       "sm_max_mhz": max(r[1] for r in self.rows), "samples": len(self.rows),
+                       "reasons": reasons}
 
 
 def distinct_rows(c):
@@ -190,7 +189,8 @@ def workload_config(w, args):
     return {"workload": w.name, "dims": list(w.dims), "nnz": w.nnz, "modes": len(w.dims), "rank": w.rank,
             "index_dist": [list(d) for d in w.index_dist], "values": list(w.values), "seed": w.seed,
             "factors": "fp32 U(0,1); bf16 variant rounded from the same draws",
-            "segment_items": args.segment_items or 1024, "l2": "inputs_exceed_l2 (no flush)",
+            "segment_items": args.segment_items or 1024, "inner_order": args.inner_order,
+            "l2": "inputs_exceed_l2 (no flush)",
             "parallelism": "single GPU per rank; ranks run independent replicas"}
 
 
@@ -270,7 +270,7 @@ def run_ours(args, w, world, rank, local, pg):
     U = distinct_rows(c)
     gen_s = time.time() - t0
     t0 = time.time()
-    t = amped.Tensor(c.dims, c.idx, c.vals, segment_items=args.segment_items)
+    t = amped.Tensor(c.dims, c.idx, c.vals, segment_items=args.segment_items, inner_order=args.inner_order)
     create_s = time.time() - t0
     stream = torch.cuda.current_stream()
     Fd = [torch.from_numpy(f).to(device) for f in F]

@@ -60,6 +60,9 @@ typedef struct {
                               amped_cp_sample); 2 = do not keep; 0 = default (keep) */
     int32_t max_rank;      /* rank the scratch is first sized for (grown on demand); default 64 */
     int32_t host_threads;  /* threads for the host reorder; 0 = all available */
+    int32_t inner_order;   /* order of the nonzeros inside an output row: 1 = caller order (stable);
+                              2 = by the coordinate of the largest other mode (better reuse of that
+                              factor's rows); 0 = default (2) */
 } amped_opts;
 
 typedef struct amped_tensor* amped_tensor_t;
@@ -75,7 +78,7 @@ typedef struct amped_tensor* amped_tensor_t;
  *   vals     host array [nnz] fp32
  *   opts     NULL for defaults
  *   out      receives the handle
- * For every mode d the nonzeros are ordered by i_d (stable), stored as
+ * For every mode d the nonzeros are ordered by i_d (inside a row as opts.inner_order says), stored as
  * struct-of-arrays (the N-1 other coordinates and the value), and cut into
  * segments of at most `segment_items` work items (one item per nonzero and
  * per output row), so a row longer than a segment is split across segments.
@@ -143,8 +146,9 @@ amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_d
 /*
  * Host-only planning query: the reorder and segment table that amped_tensor_create builds for
  * mode `mode`, without touching the GPU (for inspection and tests).  With I = dims[mode] and
- * S = ceil((I + nnz) / segment_items) (segment_items <= 0 means the default 1024):
- *   perm       [nnz]   caller index of the k-th nonzero in mode order (stable by i_mode)
+ * S = ceil((I + nnz) / segment_items) (segment_items <= 0 means the default 1024);
+ * inner_order as in amped_opts:
+ *   perm       [nnz]   caller index of the k-th nonzero in mode order
  *   rowptr     [I+1]   row i owns mode-ordered nonzeros rowptr[i] .. rowptr[i+1]-1
  *   seg_row    [S+1]   rows completed before segment s (merge-path split points)
  *   seg_nz     [S+1]   nonzeros consumed before segment s
@@ -153,7 +157,7 @@ amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_d
  * Any output pointer may be NULL to skip it.  Coordinates are validated as in create.
  */
 amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode,
-                             int segment_items, int32_t* perm, int32_t* rowptr, int32_t* seg_row, int32_t* seg_nz,
+                             int segment_items, int inner_order, int32_t* perm, int32_t* rowptr, int32_t* seg_row, int32_t* seg_nz,
                              int32_t* splits, int32_t* nsplit);
 
 /* Profiling hook: record `start` / `stop` (cudaEvent_t, may be NULL) on the call's stream

@@ -59,9 +59,18 @@ struct HostMode {
 int64_t find_bad_index(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int threads);
 
 // Stable order of the nonzeros by coordinate `mode` (two-level counting sort,
-// parallel) into hm.perm / hm.rowptr.  Returns false on allocation failure.
+// parallel) into hm.perm / hm.rowptr.  The sequence sorted is the caller
+// order, or `order[0..nnz)` when given (so sorting by a secondary key first
+// gives a lexicographic order).  Returns false on allocation failure.
 bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, int threads,
-               HostMode& hm);
+               HostMode& hm, const int32_t* order = nullptr);
+
+// The other mode whose coordinate orders nonzeros inside a row (largest dim), or -1.
+int inner_mode(int nmodes, const int64_t* dims, int mode);
+// Mode order: by i_mode, and inside a row by the inner mode's coordinate when
+// inner_sort is set (caller order otherwise); both stable.
+bool order_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, bool inner_sort,
+                int threads, HostMode& hm);
 
 // Cuts the mode-ordered copy into merge-path segments of at most `items`
 // work items (nonzeros + row ends) and derives the split-row combine tasks.

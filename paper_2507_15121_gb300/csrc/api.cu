@@ -271,7 +271,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
             return fail(AMPED_ERR_INVALID, "dims[%d]=%lld outside 1..2^31-%d", n, (long long)dims[n], 4 * kPad);
     if (nnz > 0 && (!idx || !vals)) return fail(AMPED_ERR_INVALID, "idx or vals is NULL");
     int items = 1024, threads = 0, max_rank = 64;
-    bool keep_perm = true, keep_coo = true;
+    bool keep_perm = true, keep_coo = true, inner_sort = true;
     if (opts) {
         if (opts->segment_items < 0 || opts->max_rank < 0 || opts->host_threads < 0)
             return fail(AMPED_ERR_INVALID, "negative option");
@@ -280,6 +280,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         threads = opts->host_threads;
         keep_perm = opts->keep_perm != 2;
         keep_coo = opts->keep_coo != 2;
+        inner_sort = opts->inner_order != 1;
     }
     const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, threads);
     if (bad >= 0) {
@@ -307,7 +308,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
     cudaError_t e;
     for (int mode = 0; mode < nmodes; ++mode) {
         HostMode hm;
-        if (!sort_mode(nnz, nmodes, dims, idx, mode, threads, hm) || !cut_segments(hm, items))
+        if (!order_mode(nnz, nmodes, dims, idx, mode, inner_sort, threads, hm) || !cut_segments(hm, items))
             return bail(fail(AMPED_ERR_OOM, "host allocation failed in the reorder of mode %d", mode));
         DevMode& dm = t->m[mode];
         dm.I = hm.I;
@@ -525,7 +526,7 @@ amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_d
 }
 
 amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode,
-                             int segment_items, int32_t* perm, int32_t* rowptr, int32_t* seg_row, int32_t* seg_nz,
+                             int segment_items, int inner_order, int32_t* perm, int32_t* rowptr, int32_t* seg_row, int32_t* seg_nz,
                              int32_t* splits, int32_t* nsplit) {
     g_err.clear();
     if (nmodes < 1 || nmodes > AMPED_MAX_MODES || !dims || nnz < 0 || nnz > (int64_t)INT32_MAX - 4 * kPad)
@@ -539,7 +540,7 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
     const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, 0);
     if (bad >= 0) return fail(AMPED_ERR_INDEX, "nonzero %lld has a coordinate outside dims", (long long)bad);
     HostMode hm;
-    if (!sort_mode(nnz, nmodes, dims, idx, mode, 0, hm) || !cut_segments(hm, items))
+    if (!order_mode(nnz, nmodes, dims, idx, mode, inner_order != 1, 0, hm) || !cut_segments(hm, items))
         return fail(AMPED_ERR_OOM, "host allocation failed");
     if (perm && nnz) std::memcpy(perm, hm.perm.p, (size_t)nnz * 4);
     if (rowptr) std::memcpy(rowptr, hm.rowptr.p, ((size_t)hm.I + 1) * 4);

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "amped_internal.h"
 
@@ -143,12 +144,161 @@ __device__ __forceinline__ void store_row(float* dst, const float (&a)[VEC], boo
     }
 }
 
+// ------------------------------------------------------------------ packed fp32 helpers
+// fp32 pairs in one 64-bit register for the sm_100-family packed instructions.
+__device__ __forceinline__ unsigned long long pk(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(unsigned long long r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// exact fp32 product of two bf16 / fp16 halves of 32-bit words (lo*lo, hi*hi)
+__device__ __forceinline__ void prod_bf16(uint32_t a, uint32_t b, float& lo, float& hi) {
+    asm("{ .reg .b16 al, ah, bl, bh; mov.b32 {al, ah}, %2; mov.b32 {bl, bh}, %3;\n\t"
+        "fma.rn.f32.bf16 %0, al, bl, 0f00000000; fma.rn.f32.bf16 %1, ah, bh, 0f00000000; }"
+        : "=f"(lo), "=f"(hi) : "r"(a), "r"(b));
+}
+__device__ __forceinline__ void prod_f16(uint32_t a, uint32_t b, float& lo, float& hi) {
+    asm("{ .reg .b16 al, ah, bl, bh; mov.b32 {al, ah}, %2; mov.b32 {bl, bh}, %3;\n\t"
+        "fma.rn.f32.f16 %0, al, bl, 0f00000000; fma.rn.f32.f16 %1, ah, bh, 0f00000000; }"
+        : "=f"(lo), "=f"(hi) : "r"(a), "r"(b));
+}
+
+// Raw row slices as loaded (16 bytes per lane for the vector shapes).
+template <typename T, int VEC>
+struct Raw;
+template <>
+struct Raw<float, 4> {
+    float4 v;
+    __device__ __forceinline__ void load(const float* p) {
+        asm("ld.global.nc.L1::evict_last.v4.f32 {%0,%1,%2,%3}, [%4];"
+            : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    }
+};
+template <typename H>
+struct Raw16x8 {
+    uint4 v;
+    __device__ __forceinline__ void load(const H* p) {
+        asm("ld.global.nc.L1::evict_last.v4.b32 {%0,%1,%2,%3}, [%4];"
+            : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    }
+};
+template <>
+struct Raw<__nv_bfloat16, 8> : Raw16x8<__nv_bfloat16> {};
+template <>
+struct Raw<__half, 8> : Raw16x8<__half> {};
+template <>
+struct Raw<float, 1> {
+    float f;
+    __device__ __forceinline__ void load(const float* p) { f = __ldg(p); }
+};
+template <>
+struct Raw<__nv_bfloat16, 1> {
+    float f;
+    __device__ __forceinline__ void load(const __nv_bfloat16* p) {
+        f = __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p)) << 16);
+    }
+};
+template <>
+struct Raw<__half, 1> {
+    float f;
+    __device__ __forceinline__ void load(const __half* p) { f = __half2float(__ldg(p)); }
+};
+
+__device__ __forceinline__ uint32_t w_at(const uint4& v, int i) {
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ float lo_f(uint32_t w, const __nv_bfloat16*) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float hi_f(uint32_t w, const __nv_bfloat16*) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ float lo_f(uint32_t w, const __half*) {
+    return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+}
+__device__ __forceinline__ float hi_f(uint32_t w, const __half*) {
+    return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+}
+
+// acc[e] += v * prod_n x_n[e] for the vector shapes (no staging, no masks).
+template <typename T, int VEC, int NIN>
+struct Mac;
+template <int NIN>
+struct Mac<float, 4, NIN> {
+    static __device__ __forceinline__ void run(float (&acc)[4], float v, const Raw<float, 4> (&x)[NIN]) {
+        unsigned long long p0 = pk(x[0].v.x, x[0].v.y), p1 = pk(x[0].v.z, x[0].v.w);
+#pragma unroll
+        for (int n = 1; n < NIN; ++n) {
+            p0 = mul2(p0, pk(x[n].v.x, x[n].v.y));
+            p1 = mul2(p1, pk(x[n].v.z, x[n].v.w));
+        }
+        const unsigned long long vv = pk(v, v);
+        unsigned long long a0 = fma2(vv, p0, pk(acc[0], acc[1]));
+        unsigned long long a1 = fma2(vv, p1, pk(acc[2], acc[3]));
+        upk(a0, acc[0], acc[1]);
+        upk(a1, acc[2], acc[3]);
+    }
+};
+template <typename H, int NIN>
+struct Mac16 {
+    static __device__ __forceinline__ void run(float (&acc)[8], float v, const Raw<H, 8> (&x)[NIN]) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float lo, hi;
+            if constexpr (NIN == 1) {
+                lo = lo_f(w_at(x[0].v, i), (const H*)nullptr);
+                hi = hi_f(w_at(x[0].v, i), (const H*)nullptr);
+            } else {
+                if constexpr (sizeof(H) == 2 && std::is_same<H, __nv_bfloat16>::value)
+                    prod_bf16(w_at(x[0].v, i), w_at(x[1].v, i), lo, hi);
+                else
+                    prod_f16(w_at(x[0].v, i), w_at(x[1].v, i), lo, hi);
+#pragma unroll
+                for (int n = 2; n < NIN; ++n) {
+                    lo *= lo_f(w_at(x[n].v, i), (const H*)nullptr);
+                    hi *= hi_f(w_at(x[n].v, i), (const H*)nullptr);
+                }
+            }
+            acc[2 * i] = fmaf(v, lo, acc[2 * i]);
+            acc[2 * i + 1] = fmaf(v, hi, acc[2 * i + 1]);
+        }
+    }
+};
+template <int NIN>
+struct Mac<__nv_bfloat16, 8, NIN> : Mac16<__nv_bfloat16, NIN> {};
+template <int NIN>
+struct Mac<__half, 8, NIN> : Mac16<__half, NIN> {};
+
+// Scalar (VEC = 1) shapes: one rank per lane, any R <= 32.
+template <typename T, int NIN>
+struct Mac<T, 1, NIN> {
+    static __device__ __forceinline__ void run(float (&acc)[1], float v, const Raw<T, 1> (&x)[NIN]) {
+        float pr = x[0].f;
+#pragma unroll
+        for (int n = 1; n < NIN; ++n) pr *= x[n].f;
+        acc[0] = fmaf(v, pr, acc[0]);
+    }
+};
+
 // ------------------------------------------------------------------ MTTKRP
-// Steps staged per chunk: all gathers of a chunk are issued before any use.
+// Steps per chunk: all gathers of a chunk are issued before any use.  Four
+// steps at 64 registers (4 blocks of 256 threads per SM) measured fastest on
+// GB300 for R = 32 (fp32 and bf16) against 2 or 8 steps at 2-4 blocks per SM.
 template <int VEC>
 struct Chunk {
-    static constexpr int value = VEC >= 8 ? 4 : 8;
+    static constexpr int value = 4;
 };
+
+constexpr int kBatch = 128;  // nonzeros per stream batch of a warp (32 lanes x 4)
 
 template <int NIN>
 struct StreamBatch {
@@ -172,67 +322,118 @@ __device__ __forceinline__ void load_batch(const MttkrpParams& p, int kl, uint64
     }
 }
 
+// L2 prefetch of one stream batch (NIN + 1 arrays of kBatch words = 4 lines each);
+// no registers are held, so the batch's own loads later hit L2.
+template <int NIN>
+__device__ __forceinline__ void prefetch_batch(const MttkrpParams& p, int kb, int lane) {
+    if (lane < 4 * (NIN + 1)) {
+        const int a = lane >> 2, line = lane & 3;
+        const int32_t* base = a < NIN ? p.idx[a] : (p.perm ? p.perm : reinterpret_cast<const int32_t*>(p.val));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + kb + 32 * line));
+    }
+}
+
+// Shared-memory staging of one stream batch per warp, one 16-byte record per
+// nonzero: the NIN input coordinates and the value (bit pattern) in the last word.
+// Record j lives in slot j ^ ((j >> 3) & 7): with that swizzle the staging
+// stores (lane l writes records 4l..4l+3) and the per-step loads (G consecutive
+// records) both touch every 16-byte bank group at most once per 128 bytes.
+struct WarpStage {
+    int4 rec[kBatch];
+};
+__device__ __forceinline__ int swz(int j) { return j ^ ((j >> 3) & 7); }
+
+template <int NIN>
+__device__ __forceinline__ void stage_batch(WarpStage& st, int lane, const StreamBatch<NIN>& b) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int4 r;
+        r.x = comp_rt(b.idx[0], c);
+        r.y = NIN > 1 ? comp_rt(b.idx[NIN > 1 ? 1 : 0], c) : 0;
+        r.z = NIN > 2 ? comp_rt(b.idx[NIN > 2 ? 2 : 0], c) : 0;
+        r.w = __float_as_int(comp_rt(b.val, c));
+        st.rec[swz(4 * lane + c)] = r;
+    }
+}
+
+template <int NIN>
+__device__ __forceinline__ int rec_idx(const int4& r, int n) {
+    return n == 0 ? r.x : n == 1 ? r.y : r.z;
+}
+
+// One warp processes one segment.  The warp holds G = 32/LPN groups; at
+// step u of a chunk, group g takes nonzero base + u*G + g, so all control
+// flow (batches, chunks, row ends) is uniform across the warp.  A chunk that
+// lies inside one row and inside the segment takes the fast path (no masks:
+// gathers and multiply-adds straight into the row accumulator); other chunks
+// stage their products and close rows that end inside a step with a
+// butterfly sum over the groups.
 template <typename T, int VEC, int LPN, int NIN>
-__device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, int q, unsigned wmask, bool active,
-                                               uint64_t pol) {
-    static_assert(LPN >= 2, "the rowptr window needs at least two lanes");
-    constexpr int NB = 4 * LPN;  // nonzeros per stream batch of a worker
-    constexpr int CH = Chunk<VEC>::value < NB ? Chunk<VEC>::value : NB;
-    const int R = p.R;
+__device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, WarpStage& st, int lane,
+                                               const T* const (&fl)[NIN], uint64_t pol) {
+    constexpr int G = 32 / LPN;
+    constexpr int CH = Chunk<VEC>::value;
+    constexpr int CHN = CH * G;  // nonzeros per chunk
+    static_assert(kBatch % CHN == 0, "a chunk must tile the batch");
+    const int g = lane / LPN, q = lane % LPN;
+    const bool active = q * VEC < p.R;
+    const uint32_t R = (uint32_t)p.R;
+    const int64_t rq = (int64_t)q * VEC;
     const int row_s = __ldg(p.seg_row + s), nz_s = __ldg(p.seg_nz + s);
     const int row_e = __ldg(p.seg_row + s + 1), nz_e = __ldg(p.seg_nz + s + 1);
 
-    // rowptr window: lane q holds rowptr[rwb + 4q .. rwb + 4q + 3]
-    int rwb = row_s & ~3;
-    int4 rw = __ldg(reinterpret_cast<const int4*>(p.rowptr + rwb) + q);
-    auto rowptr_at = [&](int i) -> int {
-        const int o = i - rwb;
-        return __shfl_sync(wmask, comp_rt(rw, o & 3), o >> 2, LPN);
-    };
-    auto ensure_window = [&](int i) {  // make rows i and i+1 addressable
-        if (i + 1 - rwb >= 4 * LPN) {
-            rwb = i & ~3;
-            rw = __ldg(reinterpret_cast<const int4*>(p.rowptr + rwb) + q);
+    // rowptr window of 64 rows in two registers per lane: w0 = rowptr[rwb + lane], w1 = rowptr[rwb + 32 + lane]
+    int rwb = row_s;
+    int w0 = __ldg(p.rowptr + rwb + lane);
+    int w1 = __ldg(p.rowptr + rwb + 32 + lane);
+    auto rowptr_at = [&](int r) -> int { return __shfl_sync(0xffffffffu, w0, r - rwb); };
+    auto ensure_window = [&](int r) {  // keep rows r and r+1 in w0; slide by 32 (next half prefetched)
+        if (r + 1 - rwb >= 32) {
+            rwb += 32;
+            w0 = w1;
+            w1 = __ldg(p.rowptr + rwb + 32 + lane);
         }
     };
 
     const bool cont = rowptr_at(row_s) < nz_s;  // the first row began in an earlier segment
     int i = row_s;
-    int rend;  // end of row i's nonzeros inside this segment
-    if (i < row_e) {
-        ensure_window(i);
-        rend = rowptr_at(i + 1);
-    } else {
-        rend = nz_e;
-    }
-    bool touched = false;  // row i received a nonzero in this segment
+    int rstart = nz_s;  // first nonzero of row i inside this segment
+    int rend = i < row_e ? rowptr_at(i + 1) : nz_e;  // end of row i's nonzeros inside this segment
+    const int g0 = nz_s & ~3;  // nonzero k is always processed by group (k - g0) % G
 
     float acc[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
 
-    const int64_t rq = (int64_t)q * VEC;
     auto flush = [&](int row) {
-        if (active) {
-            float* dst;
-            bool streaming = false;
-            if (row == row_s && cont) {
-                dst = p.part + ((int64_t)s * 2) * R + rq;  // head partial of a split row
-            } else if (row < row_e) {
-                dst = p.out + (int64_t)row * R + rq;  // complete row: written exactly once
-                streaming = true;
-            } else {
-                dst = p.part + ((int64_t)s * 2 + 1) * R + rq;  // tail partial of a split row
-            }
-            store_row<VEC>(dst, acc, streaming);
+        float* dst;
+        bool streaming = false;
+        if (row == row_s && cont) {
+            dst = p.part + ((int64_t)s * 2) * R + rq;  // head partial of a split row
+        } else if (row < row_e) {
+            dst = p.out + (int64_t)row * R + rq;  // complete row: written exactly once
+            streaming = true;
+        } else {
+            dst = p.part + ((int64_t)s * 2 + 1) * R + rq;  // tail partial of a split row
         }
+        const int cnt = rend - rstart;  // nonzeros of the row inside this segment
+        int owner = 0;                  // group holding the row's complete sum
+        if (cnt == 1) {
+            owner = (rstart - g0) & (G - 1);  // one contribution: it already is the sum
+        } else if (cnt > 1) {
+#pragma unroll
+            for (int o = LPN; o < 32; o <<= 1)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+        }
+        if (g == owner && active) store_row<VEC>(dst, acc, streaming);
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-        touched = false;
     };
     auto advance = [&]() {  // close row i, move to row i+1
         flush(i);
         ++i;
+        rstart = rend;
         if (i < row_e) {
             ensure_window(i);
             rend = rowptr_at(i + 1);
@@ -242,67 +443,101 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, int
     };
 
     int kb = nz_s & ~3;
-    StreamBatch<NIN> cur, nxt;
-    if (kb < nz_e) load_batch<NIN>(p, kb + 4 * q, pol, cur);
-    for (; kb < nz_e; kb += NB) {
-        if (kb + NB < nz_e) load_batch<NIN>(p, kb + NB + 4 * q, pol, nxt);  // prefetch
+    for (; kb < nz_e; kb += kBatch) {
+        {
+            StreamBatch<NIN> cur;
+            load_batch<NIN>(p, kb + 4 * lane, pol, cur);
+            __syncwarp();
+            stage_batch<NIN>(st, lane, cur);
+            __syncwarp();
+        }
+        if (kb + kBatch < nz_e) prefetch_batch<NIN>(p, kb + kBatch, lane);  // next batch into L2
 #pragma unroll 1
-        for (int j0 = 0; j0 < NB; j0 += CH) {
-            if (kb + j0 >= nz_e) break;
-            float t[CH][VEC];
+        for (int c0 = 0; c0 < kBatch; c0 += CHN) {
+            const int base = kb + c0;
+            if (base >= nz_e) break;
+            if (base + CHN <= nz_s) continue;
+            if (base >= nz_s && base + CHN <= nz_e && base + CHN <= rend) {
+                // fast path: every nonzero of the chunk is valid and in row i
+                if (active) {
 #pragma unroll
-            for (int u = 0; u < CH; ++u) {
-                const int k = kb + j0 + u;
-                const int src = (j0 + u) >> 2;  // lane holding nonzero j0+u; component u&3
-                int c[NIN];
+                    for (int u = 0; u < CH; ++u) {
+                        const int4 r = st.rec[swz(c0 + u * G + g)];
+                        Raw<T, VEC> x[NIN];
 #pragma unroll
-                for (int n = 0; n < NIN; ++n) c[n] = __shfl_sync(wmask, comp_rt(cur.idx[n], u & 3), src, LPN);
-                const float v = __shfl_sync(wmask, comp_rt(cur.val, u & 3), src, LPN);
-                const bool valid = active && k >= nz_s && k < nz_e;
+                        for (int n = 0; n < NIN; ++n) x[n].load(fl[n] + (uint64_t)(uint32_t)rec_idx<NIN>(r, n) * R);
+                        Mac<T, VEC, NIN>::run(acc, __int_as_float(r.w), x);
+                    }
+                }
+                continue;
+            }
+            // slow path, in halves of SH steps: stage masked products, then walk rows
+            constexpr int SH = CH > 4 ? 4 : CH;
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) t[u][e] = valid ? v : 0.f;
-                if (valid) {
+            for (int h = 0; h < CH; h += SH) {
+                float t[SH][VEC];
 #pragma unroll
-                    for (int n = 0; n < NIN; ++n) {
-                        float x[VEC];
-                        Row<T, VEC>::load(p.fac[n], (int64_t)c[n] * R + rq, x);
+                for (int u = 0; u < SH; ++u) {
+                    const int j = c0 + (h + u) * G + g;
+                    const int k = kb + j;
+                    const bool valid = active && k >= nz_s && k < nz_e;
+                    const int4 r = st.rec[swz(j)];
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e) t[u][e] *= x[e];
+                    for (int e = 0; e < VEC; ++e) t[u][e] = 0.f;
+                    if (valid) {
+                        Raw<T, VEC> x[NIN];
+#pragma unroll
+                        for (int n = 0; n < NIN; ++n)
+                            x[n].load(fl[n] + (uint64_t)(uint32_t)rec_idx<NIN>(r, n) * R);
+                        Mac<T, VEC, NIN>::run(t[u], __int_as_float(r.w), x);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < SH; ++u) {
+                    const int kstep = base + (h + u) * G;
+                    if (kstep >= nz_e) break;
+                    const int klast = min(kstep + G, nz_e) - 1;
+                    if (klast < nz_s) continue;
+                    if (kstep >= rstart && klast < rend) {  // the whole step lies in row i
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) acc[e] += t[u][e];
+                        continue;
+                    }
+                    const int kg = kstep + g;
+                    while (true) {
+                        const bool in = kg >= rstart && kg < rend;
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) acc[e] += in ? t[u][e] : 0.f;
+                        if (klast < rend) break;
+                        advance();
                     }
                 }
             }
-#pragma unroll
-            for (int u = 0; u < CH; ++u) {
-                const int k = kb + j0 + u;
-                if (k < nz_s || k >= nz_e) continue;
-                while (k >= rend) advance();
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) acc[e] += t[u][e];
-                touched = true;
-            }
         }
-        cur = nxt;
     }
     // close the rows that end in this segment, then the last row if it continues
     while (i < row_e) advance();
-    if (i < p.I && touched) flush(i);
+    if (i < p.I && rend > rstart) flush(i);
 }
 
 template <typename T, int VEC, int LPN, int NIN>
-__global__ void __launch_bounds__(256) mttkrp_kernel(const MttkrpParams p) {
+__global__ void __launch_bounds__(256, 4) mttkrp_kernel(const MttkrpParams p) {
+    __shared__ __align__(16) WarpStage stage[8];
     const int lane = threadIdx.x & 31;
-    const int q = lane % LPN;
-    const unsigned wmask = (LPN == 32 ? 0xffffffffu : ((1u << LPN) - 1u)) << (lane - q);
-    const bool active = q * VEC < p.R;
+    WarpStage& st = stage[threadIdx.x >> 5];
     const uint64_t pol = policy_evict_first();
+    const int q = lane % LPN;
+    const T* fl[NIN];  // this lane's first rank in every input factor
+#pragma unroll
+    for (int n = 0; n < NIN; ++n) fl[n] = static_cast<const T*>(p.fac[n]) + q * VEC;
     int s = 0;
-    if (q == 0) s = atomicAdd(p.queue, 1);
-    s = __shfl_sync(wmask, s, 0, LPN);
+    if (lane == 0) s = atomicAdd(p.queue, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
     while (s < p.S) {
         int nxt = 0;
-        if (q == 0) nxt = atomicAdd(p.queue, 1);  // next ticket, latency hidden by this segment
-        mttkrp_segment<T, VEC, LPN, NIN>(p, s, q, wmask, active, pol);
-        s = __shfl_sync(wmask, nxt, 0, LPN);
+        if (lane == 0) nxt = atomicAdd(p.queue, 1);  // next ticket, latency hidden by this segment
+        mttkrp_segment<T, VEC, LPN, NIN>(p, s, st, lane, fl, pol);
+        s = __shfl_sync(0xffffffffu, nxt, 0);
     }
 }
 

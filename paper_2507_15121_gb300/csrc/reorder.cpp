@@ -68,7 +68,7 @@ int64_t find_bad_index(int64_t nnz, int nmodes, const int64_t* dims, const int32
 }
 
 bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, int threads,
-               HostMode& hm) {
+               HostMode& hm, const int32_t* order) {
     const int64_t I = dims[mode];
     hm.mode = mode;
     hm.I = I;
@@ -84,13 +84,15 @@ bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
     std::vector<int64_t> hist((size_t)T * (size_t)B, 0);
     HostBuf<int32_t> tmp;
     if (!tmp.alloc((size_t)nnz)) return false;
+    // the sequence being sorted: caller indices 0..nnz-1, or `order` when given
+    auto elem = [&](int64_t j) -> int32_t { return order ? order[j] : (int32_t)j; };
     auto key = [&](int64_t k) -> int64_t { return idx[k * nmodes + mode]; };
 #pragma omp parallel num_threads(T)
     {
         const int t = omp_get_thread_num();
         const int64_t lo = nnz * t / T, hi = nnz * (t + 1) / T;
         int64_t* h = hist.data() + (size_t)t * B;
-        for (int64_t k = lo; k < hi; ++k) ++h[key(k) >> shift];
+        for (int64_t j = lo; j < hi; ++j) ++h[key(elem(j)) >> shift];
     }
     // exclusive scan in (bucket, thread) order keeps the scatter stable
     std::vector<int64_t> bstart((size_t)B + 1);
@@ -109,7 +111,10 @@ bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
         const int t = omp_get_thread_num();
         const int64_t lo = nnz * t / T, hi = nnz * (t + 1) / T;
         int64_t* off = hist.data() + (size_t)t * B;
-        for (int64_t k = lo; k < hi; ++k) tmp[(size_t)off[key(k) >> shift]++] = (int32_t)k;
+        for (int64_t j = lo; j < hi; ++j) {
+            const int32_t k = elem(j);
+            tmp[(size_t)off[key(k) >> shift]++] = k;
+        }
     }
     // level 2: stable counting sort of each bucket by the low bits; fills rowptr
     const int64_t span = int64_t(1) << shift;
@@ -134,6 +139,23 @@ bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
     }
     hm.rowptr[(size_t)I] = (int32_t)nnz;
     return true;
+}
+
+int inner_mode(int nmodes, const int64_t* dims, int mode) {
+    int inner = -1;
+    for (int n = 0; n < nmodes; ++n)
+        if (n != mode && (inner < 0 || dims[n] > dims[inner])) inner = n;
+    return inner;
+}
+
+bool order_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, bool inner_sort,
+                int threads, HostMode& hm) {
+    const int inner = inner_sort ? inner_mode(nmodes, dims, mode) : -1;
+    if (inner < 0) return sort_mode(nnz, nmodes, dims, idx, mode, threads, hm);
+    // lexicographic (i_mode, i_inner): sort by the inner key, then stably by i_mode
+    HostMode pre;
+    return sort_mode(nnz, nmodes, dims, idx, inner, threads, pre) &&
+           sort_mode(nnz, nmodes, dims, idx, mode, threads, hm, pre.perm.p);
 }
 
 bool cut_segments(HostMode& hm, int items) {

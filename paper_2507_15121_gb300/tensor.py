@@ -42,7 +42,7 @@ class Tensor:
     """
 
     def __init__(self, dims, idx, vals, *, segment_items: int = 0, keep_perm: bool = True, keep_coo: bool = True,
-                 max_rank: int = 0, host_threads: int = 0):
+                 max_rank: int = 0, host_threads: int = 0, inner_order: str = "lexicographic"):
         L = _lib.lib()
         self.dims = tuple(int(d) for d in dims)
         idx = np.ascontiguousarray(idx.numpy() if hasattr(idx, "numpy") else idx, dtype=np.int32)
@@ -51,7 +51,10 @@ class Tensor:
             raise ValueError("idx must be [nnz, N] and vals [nnz]")
         self.nnz = int(idx.shape[0])
         dims_a = np.asarray(self.dims, dtype=np.int64)
-        opts = _lib.Opts(segment_items, 1 if keep_perm else 2, 1 if keep_coo else 2, max_rank, host_threads)
+        if inner_order not in ("lexicographic", "stable"):
+            raise ValueError("inner_order must be 'lexicographic' or 'stable'")
+        opts = _lib.Opts(segment_items, 1 if keep_perm else 2, 1 if keep_coo else 2, max_rank, host_threads,
+                         2 if inner_order == "lexicographic" else 1)
         h = ctypes.c_void_p()
         _lib.check(L.amped_tensor_create(self.nnz, len(self.dims), dims_a.ctypes.data,
                                          idx.ctypes.data if self.nnz else None,
@@ -179,7 +182,7 @@ class Tensor:
                                                       stop.cuda_event if stop else None))
 
 
-def plan_mode(dims, idx, mode: int, segment_items: int = 0) -> dict:
+def plan_mode(dims, idx, mode: int, segment_items: int = 0, inner_order: str = "lexicographic") -> dict:
     """Host-only: the reorder and merge-path segment table for one mode."""
     L = _lib.lib()
     dims_a = np.asarray(dims, dtype=np.int64)
@@ -195,7 +198,7 @@ def plan_mode(dims, idx, mode: int, segment_items: int = 0) -> dict:
     splits = np.empty((max(S, 1), 3), np.int32)
     ns = ctypes.c_int32()
     _lib.check(L.amped_plan_mode(nnz, len(dims_a), dims_a.ctypes.data, idx.ctypes.data if nnz else None, mode,
-                                 segment_items, perm.ctypes.data, rowptr.ctypes.data, seg_row.ctypes.data,
+                                 segment_items, 2 if inner_order == "lexicographic" else 1, perm.ctypes.data, rowptr.ctypes.data, seg_row.ctypes.data,
                                  seg_nz.ctypes.data, splits.ctypes.data, ctypes.byref(ns)))
     return {"perm": perm, "rowptr": rowptr, "seg_row": seg_row, "seg_nz": seg_nz, "splits": splits[: ns.value],
             "items": items, "S": S}

@@ -68,12 +68,17 @@ def test_argument_errors_without_gpu(L):
     assert L.amped_tensor_destroy(None) == _lib.OK
 
 
-def check_plan(dims, idx, mode, items):
-    p = plan_mode(dims, idx, mode, items)
+def check_plan(dims, idx, mode, items, inner_order="lexicographic"):
+    p = plan_mode(dims, idx, mode, items, inner_order)
     nnz, I = idx.shape[0], dims[mode]
     keys = idx[:, mode]
-    # stable order by the mode's coordinate
-    np.testing.assert_array_equal(p["perm"], np.argsort(keys, kind="stable"))
+    if inner_order == "stable":  # by the mode's coordinate, ties in caller order
+        np.testing.assert_array_equal(p["perm"], np.argsort(keys, kind="stable"))
+    else:  # by (mode coordinate, coordinate of the largest other mode), ties in caller order
+        others = [n for n in range(len(dims)) if n != mode]
+        inner = max(others, key=lambda n: (dims[n], -n)) if others else None
+        order = np.lexsort((idx[:, inner], keys)) if inner is not None else np.argsort(keys, kind="stable")
+        np.testing.assert_array_equal(p["perm"], order)
     np.testing.assert_array_equal(p["rowptr"], np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=I))]))
     sr, sz, S = p["seg_row"].astype(np.int64), p["seg_nz"].astype(np.int64), p["S"]
     total = I + nnz
@@ -173,11 +178,12 @@ def make_case(name, dims, nnz, seed):
 
 @pytest.mark.parametrize("name,dims,nnz,seed", CASES)
 @pytest.mark.parametrize("items", [1, 7, 32, 1024, 10 ** 6])
-def test_plan_and_simulated_kernel_match_oracle(name, dims, nnz, seed, items):
+@pytest.mark.parametrize("inner_order", ["lexicographic", "stable"])
+def test_plan_and_simulated_kernel_match_oracle(name, dims, nnz, seed, items, inner_order):
     idx, vals = make_case(name, dims, nnz, seed)
     F = [np.random.default_rng(seed + n).uniform(0, 1, (d, 3)).astype(np.float32) for n, d in enumerate(dims)]
     for mode in range(len(dims)):
-        p = check_plan(dims, idx, mode, items)
+        p = check_plan(dims, idx, mode, items, inner_order)
         got = simulate_kernel(p, dims, idx, vals, F, mode)
         np.testing.assert_allclose(got, oracle.mttkrp(dims, idx, vals, F, mode), rtol=1e-12, atol=1e-12)
 
