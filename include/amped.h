@@ -160,6 +160,39 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
                              int segment_items, int inner_order, int32_t* perm, int32_t* rowptr, int32_t* seg_row, int32_t* seg_nz,
                              int32_t* splits, int32_t* nsplit);
 
+/*
+ * Size of the library's fixed device scratch buffer used by amped_mttkrp_noalloc (32 MiB).
+ * Every GPU that loads the library reserves this much device memory until the process exits.
+ */
+#define AMPED_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/*
+ * amped_mttkrp without any device memory allocation.  (Not from the paper: the paper has no
+ * counterpart; this is a deployment convenience of this library.)
+ *
+ * Who needs it: callers that must not allocate device memory while they run, for example code
+ * that hands every byte of the GPU to its own memory pool or arena, code with a fixed memory
+ * budget reserved up front, or a latency-sensitive loop where cudaMalloc's implicit device
+ * synchronisation is not acceptable.  amped_mttkrp may allocate (or grow) the handle's scratch
+ * on a call with a larger rank than before; this entry point never does.  It computes exactly
+ * what amped_mttkrp computes for the same arguments.
+ *
+ * Scratch: the split-row partials, their fp64 task sums and the segment ticket counter live in
+ * one static device array of AMPED_NOALLOC_SCRATCH_BYTES that the library defines.  A call whose
+ * mode needs more (4*2*S*R + 8*tasks*R bytes plus 256 for S segments and the mode's combine
+ * tasks) returns AMPED_ERR_UNSUPPORTED without launching anything; use amped_mttkrp then, or a
+ * larger segment_items at create time (fewer segments).
+ *
+ * The first call on each device looks up that device's address of the array
+ * (cudaGetSymbolAddress, with the device current); make that first call before any stream
+ * capture begins.  The array is shared by every handle and every call on the device and keeps
+ * the last call's contents (the ticket counter is cleared on the call's stream before each
+ * launch): calls that may overlap on the GPU (different streams, other threads) race on it, so
+ * serialise them.  No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+amped_status amped_mttkrp_noalloc(amped_tensor_t t, int mode, const void* const* factors, amped_dtype fdtype,
+                                  int R, float* out, void* stream);
+
 /* Profiling hook: record `start` / `stop` (cudaEvent_t, may be NULL) on the call's stream
  * immediately before and after the next MTTKRP kernel launch of this handle; cleared after use. */
 amped_status amped_set_kernel_events(amped_tensor_t t, void* start, void* stop);

@@ -50,6 +50,7 @@ def lib() -> ctypes.CDLL:
             "amped_tensor_info": ([vp, ctypes.POINTER(i64), ctypes.POINTER(c_int), vp], st),
             "amped_mttkrp": ([vp, c_int, vp, c_int, c_int, vp, vp], st),
             "amped_mttkrp_all": ([vp, vp, c_int, c_int, vp, vp], st),
+            "amped_mttkrp_noalloc": ([vp, c_int, vp, c_int, c_int, vp, vp], st),
             "amped_mttkrp_all_host": ([vp, vp, c_int, c_int, vp, vp], st),
             "amped_cp_sample": ([vp, vp, c_int, c_int, vp, vp], st),
             "amped_cp_grad": ([vp, vp, c_int, c_int, vp, vp, vp], st),

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "amped_internal.h"
@@ -565,3 +566,112 @@ amped_status amped_set_kernel_events(amped_tensor_t t, void* start, void* stop) 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free MTTKRP: the same kernels, with their scratch in a fixed
+// static device array instead of the handle's allocations.
+// ---------------------------------------------------------------------------
+namespace {
+
+// The scratch array itself.  Host code must not use this name as an address:
+// on the host it is only a stand-in; the device address comes from
+// cudaGetSymbolAddress below, looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[AMPED_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (first call per device looks it up).
+amped_status noalloc_scratch(void** addr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(AMPED_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
+        g_noalloc_addr[dev] = ptr;
+    }
+    *addr = g_noalloc_addr[dev];
+    return AMPED_OK;
+}
+
+}  // namespace
+
+extern "C" amped_status amped_mttkrp_noalloc(amped_tensor_t t, int mode, const void* const* factors,
+                                             amped_dtype fdtype, int R, float* out, void* stream) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (mode < 0 || mode >= t->N) return fail(AMPED_ERR_INVALID, "mode %d outside 0..%d", mode, t->N - 1);
+    int vec = 0;
+    amped_status s = check_call(t, factors, fdtype, R, mode, &vec);
+    if (s != AMPED_OK) return s;
+    if (t->N == 1) return fail(AMPED_ERR_UNSUPPORTED, "single-mode tensors have no MTTKRP kernel");
+    if (!out) return fail(AMPED_ERR_INVALID, "output for mode %d is NULL", mode);
+    if (!aligned(out, vec > 1 ? 16 : 4)) return fail(AMPED_ERR_INVALID, "output for mode %d is misaligned", mode);
+    const DevMode& dm = t->m[mode];
+    // layout inside the static array: ticket counter, split partials [S][2][R] fp32, task sums [tasks][R] fp64
+    const size_t part_off = 256;
+    const size_t part_bytes = (size_t)dm.S * 2 * (size_t)R * sizeof(float);
+    const size_t tsum_off = (part_off + part_bytes + 255) / 256 * 256;
+    const size_t need = tsum_off + (size_t)dm.ntask * (size_t)R * sizeof(double);
+    if (need > AMPED_NOALLOC_SCRATCH_BYTES)
+        return fail(AMPED_ERR_UNSUPPORTED,
+                    "mode %d at rank %d needs %zu bytes of scratch, more than the %u-byte static buffer; "
+                    "use amped_mttkrp or a larger segment_items",
+                    mode, R, need, (unsigned)AMPED_NOALLOC_SCRATCH_BYTES);
+    void* base = nullptr;
+    s = noalloc_scratch(&base);
+    if (s != AMPED_OK) return s;
+    unsigned char* b = static_cast<unsigned char*>(base);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(b, 0, sizeof(int), st);  // the ticket counter must start at zero
+    if (e != cudaSuccess) return cuda_fail(e, "ticket reset");
+    MttkrpParams p{};
+    p.rowptr = dm.rowptr;
+    int nin = 0;
+    for (int n = 0; n < t->N; ++n) {
+        if (n == mode) continue;
+        p.idx[nin] = dm.idx + (size_t)nin * t->stride;
+        p.fac[nin] = factors[n];
+        ++nin;
+    }
+    p.val = dm.val;
+    p.perm = nullptr;
+    p.gval = nullptr;
+    p.seg_row = dm.seg;
+    p.seg_nz = dm.seg + dm.S + 1;
+    p.out = out;
+    p.part = reinterpret_cast<float*>(b + part_off);
+    p.queue = reinterpret_cast<int*>(b);
+    p.I = (int32_t)dm.I;
+    p.S = dm.S;
+    p.R = R;
+    p.nnz = (int32_t)t->nnz;
+    int rc;
+    switch (fdtype) {
+        case AMPED_F32: rc = launch_mttkrp_f32(nin, p, 0, st); break;
+        case AMPED_BF16: rc = launch_mttkrp_bf16(nin, p, 0, st); break;
+        default: rc = launch_mttkrp_f16(nin, p, 0, st); break;
+    }
+    if (rc != 0) return cuda_fail((cudaError_t)rc, "MTTKRP kernel launch");
+    ++g_launches;
+    CombineParams c{};
+    c.tasks = dm.table;
+    c.split_info = dm.table + 4 * (size_t)dm.ntask;
+    c.multi = c.split_info + 2 * ((size_t)dm.nsplit + 1);
+    c.part = p.part;
+    c.tsum = reinterpret_cast<double*>(b + tsum_off);
+    c.out = out;
+    c.ntask = dm.ntask;
+    c.nmulti = dm.nmulti;
+    c.R = R;
+    int launched = 0;
+    rc = launch_combine(c, st, &launched);
+    g_launches += launched;
+    if (rc != 0) return cuda_fail((cudaError_t)rc, "split-row combine launch");
+    return AMPED_OK;
+}
