@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="scale nnz and dims (debug)")
     ap.add_argument("--segment-items", type=int, default=0)
     ap.add_argument("--inner-order", default="lexicographic", choices=["lexicographic", "stable"])
+    ap.add_argument("--short-rows", type=int, default=0, help="short-row threshold (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
@@ -190,6 +191,7 @@ def workload_config(w, args):
             "index_dist": [list(d) for d in w.index_dist], "values": list(w.values), "seed": w.seed,
             "factors": "fp32 U(0,1); bf16 variant rounded from the same draws",
             "segment_items": args.segment_items or 1024, "inner_order": args.inner_order,
+            "short_rows": args.short_rows or 32,
             "l2": "inputs_exceed_l2 (no flush)",
             "parallelism": "single GPU per rank; ranks run independent replicas"}
 
@@ -270,7 +272,8 @@ def run_ours(args, w, world, rank, local, pg):
     U = distinct_rows(c)
     gen_s = time.time() - t0
     t0 = time.time()
-    t = amped.Tensor(c.dims, c.idx, c.vals, segment_items=args.segment_items, inner_order=args.inner_order)
+    t = amped.Tensor(c.dims, c.idx, c.vals, segment_items=args.segment_items, inner_order=args.inner_order,
+                     short_rows=args.short_rows)
     create_s = time.time() - t0
     stream = torch.cuda.current_stream()
     Fd = [torch.from_numpy(f).to(device) for f in F]

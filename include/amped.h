@@ -63,6 +63,10 @@ typedef struct {
     int32_t inner_order;   /* order of the nonzeros inside an output row: 1 = caller order (stable);
                               2 = by the coordinate of the largest other mode (better reuse of that
                               factor's rows); 0 = default (2) */
+    int32_t short_rows;    /* rows with fewer nonzeros than this (at most 125) are "short": they are
+                              sorted by length and processed one row per lane group; longer rows are
+                              processed by whole warps along the merge path.  0 = default (32);
+                              negative = every row with a nonzero is long */
 } amped_opts;
 
 typedef struct amped_tensor* amped_tensor_t;
@@ -78,10 +82,11 @@ typedef struct amped_tensor* amped_tensor_t;
  *   vals     host array [nnz] fp32
  *   opts     NULL for defaults
  *   out      receives the handle
- * For every mode d the nonzeros are ordered by i_d (inside a row as opts.inner_order says), stored as
- * struct-of-arrays (the N-1 other coordinates and the value), and cut into
- * segments of at most `segment_items` work items (one item per nonzero and
- * per output row), so a row longer than a segment is split across segments.
+ * For every mode d the nonzeros are grouped by output row i_d (inside a row as opts.inner_order
+ * says) and stored as struct-of-arrays (the N-1 other coordinates and the value).  Rows with at
+ * least opts.short_rows nonzeros ("long") come first and are cut into merge-path segments of at
+ * most `segment_items` work items (one per nonzero and one per row end), so a row longer than a
+ * segment is split across segments; the other rows follow, sorted by length, in small segments.
  * Returns AMPED_ERR_INDEX (and names the first bad nonzero in
  * amped_last_error) when a coordinate is out of range.  The copies live on
  * the device that is current when this is called, and every later call on
@@ -143,22 +148,35 @@ amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped
 amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
                            const float* gvals, float* const* grads, void* stream);
 
+/* Sizes of a mode's plan (amped_plan_mode). */
+typedef struct {
+    int64_t nnz, rows;                    /* nonzeros; rows of the mode (dims[mode]) */
+    int64_t long_rows, long_nnz;          /* long rows and their nonzeros (copy positions 0 .. long_nnz) */
+    int64_t short_rows;                   /* short rows, including rows without nonzeros */
+    int64_t long_segments, short_segments, split_rows;
+} amped_plan_sizes;
+
 /*
- * Host-only planning query: the reorder and segment table that amped_tensor_create builds for
- * mode `mode`, without touching the GPU (for inspection and tests).  With I = dims[mode] and
- * S = ceil((I + nnz) / segment_items) (segment_items <= 0 means the default 1024);
- * inner_order as in amped_opts:
- *   perm       [nnz]   caller index of the k-th nonzero in mode order
- *   rowptr     [I+1]   row i owns mode-ordered nonzeros rowptr[i] .. rowptr[i+1]-1
- *   seg_row    [S+1]   rows completed before segment s (merge-path split points)
- *   seg_nz     [S+1]   nonzeros consumed before segment s
- *   splits     [S][3]  {row, s_a, s_b}: row straddles segment boundaries s_a..s_b
- *   nsplit     receives the number of split rows written to `splits`
- * Any output pointer may be NULL to skip it.  Coordinates are validated as in create.
+ * Host-only planning query: the reorder, row classes and segment tables that amped_tensor_create
+ * builds for mode `mode`, without touching the GPU (for inspection and tests).  segment_items,
+ * inner_order and short_rows as in amped_opts (0 = defaults).  Call once with every array NULL to
+ * read `sizes`, then again with buffers of these lengths (any may be NULL to skip it):
+ *   perm          [nnz]               caller index of the k-th nonzero of the mode's copy
+ *   rows_long     [long_rows]         row ids of the long rows (increasing)
+ *   rowptr_long   [long_rows+1]       copy positions of long row j: rowptr_long[j] .. rowptr_long[j+1]
+ *   seg_row       [long_segments+1]   long rows completed before long segment s (merge path)
+ *   seg_nz        [long_segments+1]   nonzeros consumed before long segment s
+ *   splits        [split_rows][3]     {long-row index, s_a, s_b}: the row straddles boundaries s_a..s_b
+ *   rows_short    [short_rows]        row ids of the short rows (by decreasing length)
+ *   rowptr_short  [short_rows+1]      copy positions of short row j (rowptr_short[0] = long_nnz)
+ *   seg_short     [short_segments+1]  first short row of short segment t
+ * Coordinates are validated as in create.
  */
 amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode,
-                             int segment_items, int inner_order, int32_t* perm, int32_t* rowptr, int32_t* seg_row, int32_t* seg_nz,
-                             int32_t* splits, int32_t* nsplit);
+                             int segment_items, int inner_order, int short_rows, amped_plan_sizes* sizes,
+                             int32_t* perm, int32_t* rows_long, int32_t* rowptr_long, int32_t* seg_row,
+                             int32_t* seg_nz, int32_t* splits, int32_t* rows_short, int32_t* rowptr_short,
+                             int32_t* seg_short);
 
 /*
  * Size of the library's fixed device scratch buffer used by amped_mttkrp_noalloc (32 MiB).

@@ -28,7 +28,13 @@ class AmpedError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("segment_items", ctypes.c_int32), ("keep_perm", ctypes.c_int32), ("keep_coo", ctypes.c_int32),
-                ("max_rank", ctypes.c_int32), ("host_threads", ctypes.c_int32), ("inner_order", ctypes.c_int32)]
+                ("max_rank", ctypes.c_int32), ("host_threads", ctypes.c_int32), ("inner_order", ctypes.c_int32),
+                ("short_rows", ctypes.c_int32)]
+
+
+class PlanSizes(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("nnz", "rows", "long_rows", "long_nnz", "short_rows", "long_segments",
+                                              "short_segments", "split_rows")]
 
 
 _lib = None
@@ -54,8 +60,8 @@ def lib() -> ctypes.CDLL:
             "amped_mttkrp_all_host": ([vp, vp, c_int, c_int, vp, vp], st),
             "amped_cp_sample": ([vp, vp, c_int, c_int, vp, vp], st),
             "amped_cp_grad": ([vp, vp, c_int, c_int, vp, vp, vp], st),
-            "amped_plan_mode": ([i64, c_int, vp, vp, c_int, c_int, c_int, vp, vp, vp, vp, vp, ctypes.POINTER(i32)],
-                                st),
+            "amped_plan_mode": ([i64, c_int, vp, vp, c_int, c_int, c_int, c_int, ctypes.POINTER(PlanSizes)]
+                                + [vp] * 9, st),
             "amped_set_kernel_events": ([vp, vp, vp], st),
             "amped_kernel_launches": ([], i64),
             "amped_last_error": ([], ctypes.c_char_p),

@@ -41,12 +41,23 @@ struct HostMode {
     int mode = 0;
     int64_t I = 0;                 // rows of this mode
     int64_t nnz = 0;
-    HostBuf<int32_t> perm;         // [nnz]  caller index of the k-th nonzero in mode order
-    HostBuf<int32_t> rowptr;       // [I+1]  row i owns nonzeros rowptr[i]..rowptr[i+1]-1
-    HostBuf<int32_t> seg_row;      // [S+1]  merge-path split points: rows completed before segment s
+    HostBuf<int32_t> perm;         // [nnz]  caller index of the k-th nonzero of the copy
+    HostBuf<int32_t> rowptr;       // [I+1]  before classify_rows: row i owns perm[rowptr[i] .. rowptr[i+1])
+    // After classify_rows the copy holds the long rows (>= threshold nonzeros, by
+    // increasing row id) first and then the short rows (by decreasing length).
+    int32_t L = 0;                 // long rows
+    int64_t nnz_L = 0;             // their nonzeros (copy positions 0 .. nnz_L)
+    HostBuf<int32_t> rows_L;       // [L]    row ids
+    HostBuf<int32_t> rowptr_L;     // [L+1]  copy positions of long row j: rowptr_L[j] .. rowptr_L[j+1]
+    int32_t Sr = 0;                // short rows (including rows without nonzeros)
+    HostBuf<int32_t> rows_S;       // [Sr]   row ids
+    HostBuf<int32_t> rowptr_S;     // [Sr+1] copy positions (rowptr_S[0] = nnz_L)
+    HostBuf<int32_t> seg_short;    // [S_S+1] short-row index where short segment t starts
+    int32_t S_S = 0;               // short segments
+    HostBuf<int32_t> seg_row;      // [S+1]  long merge path: long rows completed before segment s
     HostBuf<int32_t> seg_nz;       // [S+1]  nonzeros consumed before segment s
-    int32_t S = 0;                 // segments
-    HostBuf<SplitRow> splits;      // rows that straddle a segment boundary
+    int32_t S = 0;                 // long segments
+    HostBuf<SplitRow> splits;      // long rows (long-row index) that straddle a segment boundary
     int32_t nsplit = 0;
     HostBuf<int32_t> tasks;        // [ntask][4] {split id, s_lo, s_hi (exclusive), first-slot-is-tail}
     int32_t ntask = 0;
@@ -72,8 +83,19 @@ int inner_mode(int nmodes, const int64_t* dims, int mode);
 bool order_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, bool inner_sort,
                 int threads, HostMode& hm);
 
-// Cuts the mode-ordered copy into merge-path segments of at most `items`
-// work items (nonzeros + row ends) and derives the split-row combine tasks.
+// Splits the rows into long rows (at least `threshold` nonzeros; threshold
+// <= 0 makes every non-empty row long) and short rows, and rebuilds hm.perm as
+// [long rows in row-id order][short rows by decreasing length, ties by id].
+bool classify_rows(HostMode& hm, int threshold, int threads);
+
+// Most rows and nonzeros in one short segment: a short segment's nonzeros are
+// staged in one 128-entry batch, which starts up to 3 entries early.
+constexpr int kShortRows = 31;
+constexpr int kShortNnz = 124;
+
+// Cuts the long part into merge-path segments of at most `items` work items
+// (nonzeros + row ends) with the split-row combine tasks, and the short part
+// into segments of at most kShortRows rows and kShortNnz nonzeros.
 bool cut_segments(HostMode& hm, int items);
 
 // Struct-of-arrays columns of a mode-ordered copy:
@@ -87,7 +109,11 @@ void caller_column(int64_t nnz, int nmodes, const int32_t* idx, int mode, int32_
 // Device side.
 // ---------------------------------------------------------------------------
 struct MttkrpParams {
-    const int32_t* rowptr;       // [I+1] (+ slack)
+    const int32_t* rowptr;       // [L+1] copy positions of the long rows (+ slack)
+    const int32_t* rows_L;       // [L]   row ids of the long rows
+    const int32_t* rowptr_S;     // [Sr+1] copy positions of the short rows (+ slack)
+    const int32_t* rows_S;       // [Sr]  row ids of the short rows (+ slack)
+    const int32_t* seg_short;    // [S_S+1] first short row of every short segment
     const int32_t* idx[kMaxIn];  // input-mode coordinate streams in mode order (+ slack)
     const void* fac[kMaxIn];     // input-mode factors [dims][R]
     const float* val;            // values in mode order (+ slack); unused when perm != nullptr
@@ -98,7 +124,8 @@ struct MttkrpParams {
     float* out;                  // [I][R]
     float* part;                 // [S][2][R] head/tail partials of split rows
     int* queue;                  // segment ticket counter, zero at launch
-    int32_t I, S, R, nnz;
+    int32_t I, S, R, nnz;        // I: long rows; S: long segments
+    int32_t S_S;                 // short segments (tickets S .. S+S_S-1)
 };
 
 struct CombineParams {

@@ -74,15 +74,34 @@ int kernel_vec(amped_dtype dt, int R) {
 }
 
 struct DevMode {
-    int64_t I = 0;
+    int64_t I = 0;      // rows of the mode
+    int32_t L = 0;      // long rows
+    int32_t S_S = 0;    // short segments
     int32_t S = 0, nsplit = 0, ntask = 0, nmulti = 0;
-    int32_t* rowptr = nullptr;
+    int32_t* rowptr = nullptr;     // [L+1] copy positions of the long rows
+    int32_t* rows_L = nullptr;     // [L] their row ids
+    int32_t* rowptr_S = nullptr;   // [Sr+1] copy positions of the short rows
+    int32_t* rows_S = nullptr;     // [Sr] their row ids
+    int32_t* seg_short = nullptr;  // [S_S+1]
     int32_t* idx = nullptr;  // N-1 streams of `stride` elements
     float* val = nullptr;
     int32_t* perm = nullptr;
     int32_t* seg = nullptr;   // seg_row [S+1], then seg_nz [S+1]
     int32_t* table = nullptr; // tasks [4*ntask], split_info [2*(nsplit+1)], multi [nmulti]
+    int slot_mode[AMPED_MAX_MODES] = {};  // input slot -> tensor mode; slot 0 is the inner-order mode
 };
+
+// Input slots of a mode copy: the mode that orders nonzeros inside a row first
+// (the kernel reuses its factor rows across consecutive nonzeros), then the
+// other modes in increasing order.
+int input_slots(int nmodes, const int64_t* dims, int mode, bool inner_sort, int* slot_mode) {
+    int nin = 0;
+    const int inner = inner_sort ? inner_mode(nmodes, dims, mode) : -1;
+    if (inner >= 0) slot_mode[nin++] = inner;
+    for (int n = 0; n < nmodes; ++n)
+        if (n != mode && n != inner) slot_mode[nin++] = n;
+    return nin;
+}
 
 }  // namespace
 
@@ -200,12 +219,15 @@ amped_status run_mode(amped_tensor* t, int mode, const void* const* factors, amp
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
     MttkrpParams p{};
     p.rowptr = dm.rowptr;
-    int nin = 0;
-    for (int n = 0; n < t->N; ++n) {
-        if (n == mode) continue;
-        p.idx[nin] = dm.idx + (size_t)nin * t->stride;
-        p.fac[nin] = factors[n];
-        ++nin;
+    p.rows_L = dm.rows_L;
+    p.rowptr_S = dm.rowptr_S;
+    p.rows_S = dm.rows_S;
+    p.seg_short = dm.seg_short;
+    p.S_S = dm.S_S;
+    const int nin = t->N - 1;
+    for (int slot = 0; slot < nin; ++slot) {
+        p.idx[slot] = dm.idx + (size_t)slot * t->stride;
+        p.fac[slot] = factors[dm.slot_mode[slot]];
     }
     p.val = dm.val;
     p.perm = gval ? dm.perm : nullptr;
@@ -215,7 +237,7 @@ amped_status run_mode(amped_tensor* t, int mode, const void* const* factors, amp
     p.out = out;
     p.part = t->part;
     p.queue = t->queue;
-    p.I = (int32_t)dm.I;
+    p.I = dm.L;
     p.S = dm.S;
     p.R = R;
     p.nnz = (int32_t)t->nnz;
@@ -271,7 +293,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         if (dims[n] < 1 || dims[n] > (int64_t)INT32_MAX - 4 * kPad)
             return fail(AMPED_ERR_INVALID, "dims[%d]=%lld outside 1..2^31-%d", n, (long long)dims[n], 4 * kPad);
     if (nnz > 0 && (!idx || !vals)) return fail(AMPED_ERR_INVALID, "idx or vals is NULL");
-    int items = 1024, threads = 0, max_rank = 64;
+    int items = 1024, threads = 0, max_rank = 64, short_thr = 32;
     bool keep_perm = true, keep_coo = true, inner_sort = true;
     if (opts) {
         if (opts->segment_items < 0 || opts->max_rank < 0 || opts->host_threads < 0)
@@ -282,6 +304,8 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         keep_perm = opts->keep_perm != 2;
         keep_coo = opts->keep_coo != 2;
         inner_sort = opts->inner_order != 1;
+        if (opts->short_rows > 0) short_thr = std::min(opts->short_rows, kShortNnz + 1);
+        if (opts->short_rows < 0) short_thr = 1;  // every non-empty row takes the long path
     }
     const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, threads);
     if (bad >= 0) {
@@ -309,28 +333,33 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
     cudaError_t e;
     for (int mode = 0; mode < nmodes; ++mode) {
         HostMode hm;
-        if (!order_mode(nnz, nmodes, dims, idx, mode, inner_sort, threads, hm) || !cut_segments(hm, items))
+        if (!order_mode(nnz, nmodes, dims, idx, mode, inner_sort, threads, hm) ||
+            !classify_rows(hm, short_thr, threads) || !cut_segments(hm, items))
             return bail(fail(AMPED_ERR_OOM, "host allocation failed in the reorder of mode %d", mode));
         DevMode& dm = t->m[mode];
         dm.I = hm.I;
+        dm.L = hm.L;
+        dm.S_S = hm.S_S;
         dm.S = hm.S;
         dm.nsplit = hm.nsplit;
         dm.ntask = hm.ntask;
         dm.nmulti = hm.nmulti;
-        if ((e = upload(t, &dm.rowptr, hm.rowptr.p, (size_t)hm.I + 1, (size_t)hm.I + 1 + kPad)) != cudaSuccess)
-            return bail(cuda_fail(e, "device copy of the row pointers"));
+        if ((e = upload(t, &dm.rowptr, hm.rowptr_L.p, (size_t)hm.L + 1, (size_t)hm.L + 1 + kPad)) != cudaSuccess ||
+            (e = upload(t, &dm.rows_L, hm.rows_L.p, (size_t)hm.L, (size_t)hm.L + kPad)) != cudaSuccess ||
+            (e = upload(t, &dm.rowptr_S, hm.rowptr_S.p, (size_t)hm.Sr + 1, (size_t)hm.Sr + 1 + kPad)) != cudaSuccess ||
+            (e = upload(t, &dm.rows_S, hm.rows_S.p, (size_t)hm.Sr, (size_t)hm.Sr + kPad)) != cudaSuccess ||
+            (e = upload(t, &dm.seg_short, hm.seg_short.p, (size_t)hm.S_S + 1, (size_t)hm.S_S + 1)) != cudaSuccess)
+            return bail(cuda_fail(e, "device copy of the row tables"));
         if (nmodes > 1) {
             if ((e = t->dalloc(reinterpret_cast<void**>(&dm.idx), (size_t)(nmodes - 1) * stride * 4)) != cudaSuccess)
                 return bail(cuda_fail(e, "device copy of the coordinates"));
-            int slot = 0;
-            for (int n = 0; n < nmodes; ++n) {
-                if (n == mode) continue;
-                gather_column(hm, nmodes, idx, n, col.p, threads);
+            const int nin = input_slots(nmodes, dims, mode, inner_sort, dm.slot_mode);
+            for (int slot = 0; slot < nin; ++slot) {
+                gather_column(hm, nmodes, idx, dm.slot_mode[slot], col.p, threads);
                 std::memset(col.p + nnz, 0, (stride - (size_t)nnz) * 4);
                 if ((e = cudaMemcpy(dm.idx + (size_t)slot * stride, col.p, stride * 4, cudaMemcpyHostToDevice)) !=
                     cudaSuccess)
                     return bail(cuda_fail(e, "device copy of the coordinates"));
-                ++slot;
             }
         }
         gather_values(hm, vals, fcol.p, threads);
@@ -527,8 +556,10 @@ amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_d
 }
 
 amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode,
-                             int segment_items, int inner_order, int32_t* perm, int32_t* rowptr, int32_t* seg_row, int32_t* seg_nz,
-                             int32_t* splits, int32_t* nsplit) {
+                             int segment_items, int inner_order, int short_rows, amped_plan_sizes* sizes,
+                             int32_t* perm, int32_t* rows_long, int32_t* rowptr_long, int32_t* seg_row,
+                             int32_t* seg_nz, int32_t* splits, int32_t* rows_short, int32_t* rowptr_short,
+                             int32_t* seg_short) {
     g_err.clear();
     if (nmodes < 1 || nmodes > AMPED_MAX_MODES || !dims || nnz < 0 || nnz > (int64_t)INT32_MAX - 4 * kPad)
         return fail(AMPED_ERR_INVALID, "bad tensor shape");
@@ -538,13 +569,26 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
             return fail(AMPED_ERR_INVALID, "dims[%d]=%lld out of range", n, (long long)dims[n]);
     if (nnz > 0 && !idx) return fail(AMPED_ERR_INVALID, "idx is NULL");
     const int items = segment_items > 0 ? segment_items : 1024;
+    const int thr = short_rows > 0 ? std::min(short_rows, kShortNnz + 1) : short_rows < 0 ? 1 : 32;
     const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, 0);
     if (bad >= 0) return fail(AMPED_ERR_INDEX, "nonzero %lld has a coordinate outside dims", (long long)bad);
     HostMode hm;
-    if (!order_mode(nnz, nmodes, dims, idx, mode, inner_order != 1, 0, hm) || !cut_segments(hm, items))
+    if (!order_mode(nnz, nmodes, dims, idx, mode, inner_order != 1, 0, hm) || !classify_rows(hm, thr, 0) ||
+        !cut_segments(hm, items))
         return fail(AMPED_ERR_OOM, "host allocation failed");
+    if (sizes) {
+        sizes->nnz = nnz;
+        sizes->rows = hm.I;
+        sizes->long_rows = hm.L;
+        sizes->long_nnz = hm.nnz_L;
+        sizes->short_rows = hm.Sr;
+        sizes->long_segments = hm.S;
+        sizes->short_segments = hm.S_S;
+        sizes->split_rows = hm.nsplit;
+    }
     if (perm && nnz) std::memcpy(perm, hm.perm.p, (size_t)nnz * 4);
-    if (rowptr) std::memcpy(rowptr, hm.rowptr.p, ((size_t)hm.I + 1) * 4);
+    if (rows_long && hm.L) std::memcpy(rows_long, hm.rows_L.p, (size_t)hm.L * 4);
+    if (rowptr_long) std::memcpy(rowptr_long, hm.rowptr_L.p, ((size_t)hm.L + 1) * 4);
     if (seg_row) std::memcpy(seg_row, hm.seg_row.p, ((size_t)hm.S + 1) * 4);
     if (seg_nz) std::memcpy(seg_nz, hm.seg_nz.p, ((size_t)hm.S + 1) * 4);
     if (splits)
@@ -553,7 +597,9 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
             splits[3 * j + 1] = hm.splits[(size_t)j].s_a;
             splits[3 * j + 2] = hm.splits[(size_t)j].s_b;
         }
-    if (nsplit) *nsplit = hm.nsplit;
+    if (rows_short && hm.Sr) std::memcpy(rows_short, hm.rows_S.p, (size_t)hm.Sr * 4);
+    if (rowptr_short) std::memcpy(rowptr_short, hm.rowptr_S.p, ((size_t)hm.Sr + 1) * 4);
+    if (seg_short) std::memcpy(seg_short, hm.seg_short.p, ((size_t)hm.S_S + 1) * 4);
     return AMPED_OK;
 }
 
@@ -632,12 +678,15 @@ extern "C" amped_status amped_mttkrp_noalloc(amped_tensor_t t, int mode, const v
     if (e != cudaSuccess) return cuda_fail(e, "ticket reset");
     MttkrpParams p{};
     p.rowptr = dm.rowptr;
-    int nin = 0;
-    for (int n = 0; n < t->N; ++n) {
-        if (n == mode) continue;
-        p.idx[nin] = dm.idx + (size_t)nin * t->stride;
-        p.fac[nin] = factors[n];
-        ++nin;
+    p.rows_L = dm.rows_L;
+    p.rowptr_S = dm.rowptr_S;
+    p.rows_S = dm.rows_S;
+    p.seg_short = dm.seg_short;
+    p.S_S = dm.S_S;
+    const int nin = t->N - 1;
+    for (int slot = 0; slot < nin; ++slot) {
+        p.idx[slot] = dm.idx + (size_t)slot * t->stride;
+        p.fac[slot] = factors[dm.slot_mode[slot]];
     }
     p.val = dm.val;
     p.perm = nullptr;
@@ -647,7 +696,7 @@ extern "C" amped_status amped_mttkrp_noalloc(amped_tensor_t t, int mode, const v
     p.out = out;
     p.part = reinterpret_cast<float*>(b + part_off);
     p.queue = reinterpret_cast<int*>(b);
-    p.I = (int32_t)dm.I;
+    p.I = dm.L;
     p.S = dm.S;
     p.R = R;
     p.nnz = (int32_t)t->nnz;

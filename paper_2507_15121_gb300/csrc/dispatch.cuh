@@ -24,10 +24,10 @@ static int device_sms() {
     return sms > 0 ? sms : 1;
 }
 
-// Vector width for a (dtype, R): 16-byte rows slices when R allows, else scalar.
+// Vector width for a (dtype, R): 32-byte row slices when R allows, else scalar.
 template <typename T>
 struct Shape {
-    static constexpr int kVec = sizeof(T) == 4 ? 4 : 8;
+    static constexpr int kVec = 32 / (int)sizeof(T);
     static int vec(int R) { return (R % kVec == 0 && R <= 32 * kVec) ? kVec : (R <= 32 ? 1 : 0); }
     // Lanes per worker: a power of two >= 2 (the rowptr window of a worker
     // must hold rows i and i+1 after a reload at i & ~3, which needs 8 entries).

@@ -62,71 +62,6 @@ __device__ __forceinline__ float comp_rt(const float4& v, int c) {
     return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
 }
 
-// Factor-row gather: VEC consecutive entries of type T widened to fp32.
-template <typename T, int VEC>
-struct Row;
-
-template <>
-struct Row<float, 4> {
-    static __device__ __forceinline__ void load(const void* base, int64_t off, float (&x)[4]) {
-        const float* p = static_cast<const float*>(base) + off;
-        asm("ld.global.nc.L1::evict_last.v4.f32 {%0,%1,%2,%3}, [%4];"
-            : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3])
-            : "l"(p));
-    }
-};
-template <>
-struct Row<float, 1> {
-    static __device__ __forceinline__ void load(const void* base, int64_t off, float (&x)[1]) {
-        x[0] = __ldg(static_cast<const float*>(base) + off);
-    }
-};
-template <>
-struct Row<__nv_bfloat16, 8> {
-    static __device__ __forceinline__ void load(const void* base, int64_t off, float (&x)[8]) {
-        const __nv_bfloat16* p = static_cast<const __nv_bfloat16*>(base) + off;
-        uint32_t w[4];
-        asm("ld.global.nc.L1::evict_last.v4.b32 {%0,%1,%2,%3}, [%4];"
-            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
-            : "l"(p));
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {  // bf16 is the high half of an fp32
-            x[2 * i] = __uint_as_float(w[i] << 16);
-            x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
-        }
-    }
-};
-template <>
-struct Row<__nv_bfloat16, 1> {
-    static __device__ __forceinline__ void load(const void* base, int64_t off, float (&x)[1]) {
-        const unsigned short* p = static_cast<const unsigned short*>(base) + off;
-        x[0] = __uint_as_float((uint32_t)__ldg(p) << 16);
-    }
-};
-template <>
-struct Row<__half, 8> {
-    static __device__ __forceinline__ void load(const void* base, int64_t off, float (&x)[8]) {
-        const __half* p = static_cast<const __half*>(base) + off;
-        uint32_t w[4];
-        asm("ld.global.nc.L1::evict_last.v4.b32 {%0,%1,%2,%3}, [%4];"
-            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
-            : "l"(p));
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __half2 h = *reinterpret_cast<__half2*>(&w[i]);
-            float2 f = __half22float2(h);
-            x[2 * i] = f.x;
-            x[2 * i + 1] = f.y;
-        }
-    }
-};
-template <>
-struct Row<__half, 1> {
-    static __device__ __forceinline__ void load(const void* base, int64_t off, float (&x)[1]) {
-        x[0] = __half2float(__ldg(static_cast<const __half*>(base) + off));
-    }
-};
-
 template <int VEC>
 __device__ __forceinline__ void store_row(float* dst, const float (&a)[VEC], bool streaming) {
     if constexpr (VEC % 4 == 0) {
@@ -176,29 +111,30 @@ __device__ __forceinline__ void prod_f16(uint32_t a, uint32_t b, float& lo, floa
         : "=f"(lo), "=f"(hi) : "r"(a), "r"(b));
 }
 
-// Raw row slices as loaded (16 bytes per lane for the vector shapes).
+// Raw row slices as loaded: 32 bytes per lane for the vector shapes (one
+// 256-bit load; four lanes cover a 128-byte row of 32 fp32 or 64 16-bit values).
+__device__ __forceinline__ void ld_v8(const void* p, uint32_t (&w)[8]) {
+    asm("ld.global.nc.L1::evict_last.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+        : "l"(p));
+}
 template <typename T, int VEC>
 struct Raw;
 template <>
-struct Raw<float, 4> {
-    float4 v;
-    __device__ __forceinline__ void load(const float* p) {
-        asm("ld.global.nc.L1::evict_last.v4.f32 {%0,%1,%2,%3}, [%4];"
-            : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-    }
-};
-template <typename H>
-struct Raw16x8 {
-    uint4 v;
-    __device__ __forceinline__ void load(const H* p) {
-        asm("ld.global.nc.L1::evict_last.v4.b32 {%0,%1,%2,%3}, [%4];"
-            : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
-    }
+struct Raw<float, 8> {
+    uint32_t w[8];
+    __device__ __forceinline__ void load(const float* p) { ld_v8(p, w); }
 };
 template <>
-struct Raw<__nv_bfloat16, 8> : Raw16x8<__nv_bfloat16> {};
+struct Raw<__nv_bfloat16, 16> {
+    uint32_t w[8];
+    __device__ __forceinline__ void load(const __nv_bfloat16* p) { ld_v8(p, w); }
+};
 template <>
-struct Raw<__half, 8> : Raw16x8<__half> {};
+struct Raw<__half, 16> {
+    uint32_t w[8];
+    __device__ __forceinline__ void load(const __half* p) { ld_v8(p, w); }
+};
 template <>
 struct Raw<float, 1> {
     float f;
@@ -217,9 +153,6 @@ struct Raw<__half, 1> {
     __device__ __forceinline__ void load(const __half* p) { f = __half2float(__ldg(p)); }
 };
 
-__device__ __forceinline__ uint32_t w_at(const uint4& v, int i) {
-    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
-}
 __device__ __forceinline__ float lo_f(uint32_t w, const __nv_bfloat16*) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float hi_f(uint32_t w, const __nv_bfloat16*) { return __uint_as_float(w & 0xffff0000u); }
 __device__ __forceinline__ float lo_f(uint32_t w, const __half*) {
@@ -233,39 +166,38 @@ __device__ __forceinline__ float hi_f(uint32_t w, const __half*) {
 template <typename T, int VEC, int NIN>
 struct Mac;
 template <int NIN>
-struct Mac<float, 4, NIN> {
-    static __device__ __forceinline__ void run(float (&acc)[4], float v, const Raw<float, 4> (&x)[NIN]) {
-        unsigned long long p0 = pk(x[0].v.x, x[0].v.y), p1 = pk(x[0].v.z, x[0].v.w);
-#pragma unroll
-        for (int n = 1; n < NIN; ++n) {
-            p0 = mul2(p0, pk(x[n].v.x, x[n].v.y));
-            p1 = mul2(p1, pk(x[n].v.z, x[n].v.w));
-        }
+struct Mac<float, 8, NIN> {  // packed f32x2: four pairs per lane
+    static __device__ __forceinline__ void run(float (&acc)[8], float v, const Raw<float, 8> (&x)[NIN]) {
         const unsigned long long vv = pk(v, v);
-        unsigned long long a0 = fma2(vv, p0, pk(acc[0], acc[1]));
-        unsigned long long a1 = fma2(vv, p1, pk(acc[2], acc[3]));
-        upk(a0, acc[0], acc[1]);
-        upk(a1, acc[2], acc[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            unsigned long long pr = pk(__uint_as_float(x[0].w[2 * k]), __uint_as_float(x[0].w[2 * k + 1]));
+#pragma unroll
+            for (int n = 1; n < NIN; ++n)
+                pr = mul2(pr, pk(__uint_as_float(x[n].w[2 * k]), __uint_as_float(x[n].w[2 * k + 1])));
+            unsigned long long a = fma2(vv, pr, pk(acc[2 * k], acc[2 * k + 1]));
+            upk(a, acc[2 * k], acc[2 * k + 1]);
+        }
     }
 };
 template <typename H, int NIN>
-struct Mac16 {
-    static __device__ __forceinline__ void run(float (&acc)[8], float v, const Raw<H, 8> (&x)[NIN]) {
+struct Mac16 {  // 16-bit factors: exact fp32 products of the first two, fp32 for the rest
+    static __device__ __forceinline__ void run(float (&acc)[16], float v, const Raw<H, 16> (&x)[NIN]) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 8; ++i) {
             float lo, hi;
             if constexpr (NIN == 1) {
-                lo = lo_f(w_at(x[0].v, i), (const H*)nullptr);
-                hi = hi_f(w_at(x[0].v, i), (const H*)nullptr);
+                lo = lo_f(x[0].w[i], (const H*)nullptr);
+                hi = hi_f(x[0].w[i], (const H*)nullptr);
             } else {
-                if constexpr (sizeof(H) == 2 && std::is_same<H, __nv_bfloat16>::value)
-                    prod_bf16(w_at(x[0].v, i), w_at(x[1].v, i), lo, hi);
+                if constexpr (std::is_same<H, __nv_bfloat16>::value)
+                    prod_bf16(x[0].w[i], x[1].w[i], lo, hi);
                 else
-                    prod_f16(w_at(x[0].v, i), w_at(x[1].v, i), lo, hi);
+                    prod_f16(x[0].w[i], x[1].w[i], lo, hi);
 #pragma unroll
                 for (int n = 2; n < NIN; ++n) {
-                    lo *= lo_f(w_at(x[n].v, i), (const H*)nullptr);
-                    hi *= hi_f(w_at(x[n].v, i), (const H*)nullptr);
+                    lo *= lo_f(x[n].w[i], (const H*)nullptr);
+                    hi *= hi_f(x[n].w[i], (const H*)nullptr);
                 }
             }
             acc[2 * i] = fmaf(v, lo, acc[2 * i]);
@@ -274,9 +206,9 @@ struct Mac16 {
     }
 };
 template <int NIN>
-struct Mac<__nv_bfloat16, 8, NIN> : Mac16<__nv_bfloat16, NIN> {};
+struct Mac<__nv_bfloat16, 16, NIN> : Mac16<__nv_bfloat16, NIN> {};
 template <int NIN>
-struct Mac<__half, 8, NIN> : Mac16<__half, NIN> {};
+struct Mac<__half, 16, NIN> : Mac16<__half, NIN> {};
 
 // Scalar (VEC = 1) shapes: one rank per lane, any R <= 32.
 template <typename T, int NIN>
@@ -289,13 +221,77 @@ struct Mac<T, 1, NIN> {
     }
 };
 
+// Widen a raw row slice to fp32.
+__device__ __forceinline__ void widen(const Raw<float, 8>& r, float (&x)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = __uint_as_float(r.w[i]);
+}
+template <typename H>
+__device__ __forceinline__ void widen(const Raw<H, 16>& r, float (&x)[16]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        x[2 * i] = lo_f(r.w[i], (const H*)nullptr);
+        x[2 * i + 1] = hi_f(r.w[i], (const H*)nullptr);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void widen(const Raw<T, 1>& r, float (&x)[1]) {
+    x[0] = r.f;
+}
+
+// Reduce-scatter of VEC-wide partial rows over the G groups of a warp (lanes
+// q, q+LPN, q+2LPN, ... hold the same ranks): after log2(G) halving rounds
+// each lane holds VEC/G summed ranks starting at the returned offset.
+template <int VEC, int G, int LPN>
+__device__ __forceinline__ int reduce_scatter(float (&a)[VEC], int g) {
+    int e0 = 0;
+#pragma unroll
+    for (int k = 0; (1 << k) < G; ++k) {
+        const int c = VEC >> k;
+        const int bit = (g >> k) & 1;
+#pragma unroll
+        for (int i = 0; i < c / 2; ++i) {
+            const float keep = bit ? a[c / 2 + i] : a[i];
+            const float send = bit ? a[i] : a[c / 2 + i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, LPN << k);
+        }
+        e0 += bit * (c / 2);
+    }
+    return e0;
+}
+
+template <int M, int VEC>
+__device__ __forceinline__ void store_part(float* dst, const float (&a)[VEC], bool streaming) {
+    if constexpr (M >= 4) {
+#pragma unroll
+        for (int i = 0; i < M; i += 4) {
+            const float4 v = make_float4(a[i], a[i + 1], a[i + 2], a[i + 3]);
+            if (streaming)
+                __stcs(reinterpret_cast<float4*>(dst + i), v);
+            else
+                *reinterpret_cast<float4*>(dst + i) = v;
+        }
+    } else if constexpr (M == 2) {
+        const float2 v = make_float2(a[0], a[1]);
+        if (streaming)
+            __stcs(reinterpret_cast<float2*>(dst), v);
+        else
+            *reinterpret_cast<float2*>(dst) = v;
+    } else {
+        if (streaming)
+            __stcs(dst, a[0]);
+        else
+            *dst = a[0];
+    }
+}
+
 // ------------------------------------------------------------------ MTTKRP
 // Steps per chunk: all gathers of a chunk are issued before any use.  Four
 // steps at 64 registers (4 blocks of 256 threads per SM) measured fastest on
 // GB300 for R = 32 (fp32 and bf16) against 2 or 8 steps at 2-4 blocks per SM.
 template <int VEC>
 struct Chunk {
-    static constexpr int value = 4;
+    static constexpr int value = VEC >= 8 ? 2 : 4;
 };
 
 constexpr int kBatch = 128;  // nonzeros per stream batch of a warp (32 lanes x 4)
@@ -307,7 +303,8 @@ struct StreamBatch {
 };
 
 template <int NIN>
-__device__ __forceinline__ void load_batch(const MttkrpParams& p, int kl, uint64_t pol, StreamBatch<NIN>& b) {
+__device__ __forceinline__ void load_batch(const MttkrpParams& p, int kl, StreamBatch<NIN>& b) {
+    const uint64_t pol = policy_evict_first();
 #pragma unroll
     for (int n = 0; n < NIN; ++n) b.idx[n] = ld_stream_i4(p.idx[n] + kl, pol);
     if (p.perm == nullptr) {
@@ -370,7 +367,7 @@ __device__ __forceinline__ int rec_idx(const int4& r, int n) {
 // butterfly sum over the groups.
 template <typename T, int VEC, int LPN, int NIN>
 __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, WarpStage& st, int lane,
-                                               const T* const (&fl)[NIN], uint64_t pol) {
+                                               const T* const (&fl)[NIN]) {
     constexpr int G = 32 / LPN;
     constexpr int CH = Chunk<VEC>::value;
     constexpr int CHN = CH * G;  // nonzeros per chunk
@@ -378,7 +375,6 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
     const int g = lane / LPN, q = lane % LPN;
     const bool active = q * VEC < p.R;
     const uint32_t R = (uint32_t)p.R;
-    const int64_t rq = (int64_t)q * VEC;
     const int row_s = __ldg(p.seg_row + s), nz_s = __ldg(p.seg_nz + s);
     const int row_e = __ldg(p.seg_row + s + 1), nz_e = __ldg(p.seg_nz + s + 1);
 
@@ -399,34 +395,41 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
     int i = row_s;
     int rstart = nz_s;  // first nonzero of row i inside this segment
     int rend = i < row_e ? rowptr_at(i + 1) : nz_e;  // end of row i's nonzeros inside this segment
-    const int g0 = nz_s & ~3;  // nonzero k is always processed by group (k - g0) % G
 
     float acc[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
 
     auto flush = [&](int row) {
+        const int64_t rq = (int64_t)(lane % LPN) * VEC;
         float* dst;
         bool streaming = false;
         if (row == row_s && cont) {
             dst = p.part + ((int64_t)s * 2) * R + rq;  // head partial of a split row
         } else if (row < row_e) {
-            dst = p.out + (int64_t)row * R + rq;  // complete row: written exactly once
+            dst = p.out + (int64_t)__ldg(p.rows_L + row) * R + rq;  // complete row: written exactly once
             streaming = true;
         } else {
             dst = p.part + ((int64_t)s * 2 + 1) * R + rq;  // tail partial of a split row
         }
         const int cnt = rend - rstart;  // nonzeros of the row inside this segment
-        int owner = 0;                  // group holding the row's complete sum
-        if (cnt == 1) {
-            owner = (rstart - g0) & (G - 1);  // one contribution: it already is the sum
-        } else if (cnt > 1) {
+        if (cnt > 1 && G > 1 && G <= VEC) {
+            // reduce-scatter over the G groups: each lane ends with VEC/G summed ranks
+            const int e0 = reduce_scatter<VEC, G, LPN>(acc, g);
+            if (active) store_part<VEC / G>(dst + e0, acc, streaming);
+        } else {
+            int owner = 0;  // group holding the row's complete sum
+            if (cnt == 1) {
+                // one contribution, already the sum; nonzero k is always processed by group (k - (nz_s & ~3)) % G
+                owner = (rstart - (nz_s & ~3)) & (G - 1);
+            } else if (cnt > 1) {
 #pragma unroll
-            for (int o = LPN; o < 32; o <<= 1)
+                for (int o = LPN; o < 32; o <<= 1)
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+                    for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+            }
+            if (g == owner && active) store_row<VEC>(dst, acc, streaming);
         }
-        if (g == owner && active) store_row<VEC>(dst, acc, streaming);
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
     };
@@ -446,7 +449,7 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
     for (; kb < nz_e; kb += kBatch) {
         {
             StreamBatch<NIN> cur;
-            load_batch<NIN>(p, kb + 4 * lane, pol, cur);
+            load_batch<NIN>(p, kb + 4 * lane, cur);
             __syncwarp();
             stage_batch<NIN>(st, lane, cur);
             __syncwarp();
@@ -520,23 +523,75 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
     if (i < p.I && rend > rstart) flush(i);
 }
 
+// One short segment: at most kShortRows rows (sorted by length, so rows of a
+// round have similar lengths) whose nonzeros fit one staged batch.  Group g
+// accumulates row r0+g by itself and stores it: no cross-group reduction.
+template <typename T, int VEC, int LPN, int NIN>
+__device__ __forceinline__ void mttkrp_short(const MttkrpParams& p, int t, WarpStage& st, int lane,
+                                             const T* const (&fl)[NIN]) {
+    constexpr int G = 32 / LPN;
+    const int g = lane / LPN, q = lane % LPN;
+    const bool active = q * VEC < p.R;
+    const uint32_t R = (uint32_t)p.R;
+    const int a = __ldg(p.seg_short + t), nr = __ldg(p.seg_short + t + 1) - a;  // nr <= 31
+    const int my_rp = __ldg(p.rowptr_S + a + min(lane, nr));  // lane l: start of short row a+l; lane nr: end
+    const int my_id = lane < nr ? __ldg(p.rows_S + a + lane) : 0;
+    const int k0 = __shfl_sync(0xffffffffu, my_rp, 0), k1 = __shfl_sync(0xffffffffu, my_rp, nr);
+    const int kb = k0 & ~3;  // k1 - kb < kBatch by construction of the short segments
+    if (k1 > k0) {
+        StreamBatch<NIN> cur;
+        load_batch<NIN>(p, kb + 4 * lane, cur);
+        __syncwarp();
+        stage_batch<NIN>(st, lane, cur);
+        __syncwarp();
+    }
+    for (int r0 = 0; r0 < nr; r0 += G) {
+        const int rr = r0 + g;
+        const int start = __shfl_sync(0xffffffffu, my_rp, min(rr, nr));
+        const int end = __shfl_sync(0xffffffffu, my_rp, min(rr + 1, nr));
+        const int len = rr < nr ? end - start : 0;
+        const int maxlen = __reduce_max_sync(0xffffffffu, len);
+        float acc[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+        for (int k = 0; k < maxlen; k += 2) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (active && k + u < len) {
+                    const int4 r = st.rec[swz(start + k + u - kb)];
+                    Raw<T, VEC> x[NIN];
+#pragma unroll
+                    for (int n = 0; n < NIN; ++n) x[n].load(fl[n] + (uint64_t)(uint32_t)rec_idx<NIN>(r, n) * R);
+                    Mac<T, VEC, NIN>::run(acc, __int_as_float(r.w), x);
+                }
+            }
+        }
+        const int id = __shfl_sync(0xffffffffu, my_id, rr & 31);
+        if (rr < nr && active) store_row<VEC>(p.out + (int64_t)id * R + q * VEC, acc, true);
+    }
+    __syncwarp();  // the stage is reused by the warp's next segment
+}
+
 template <typename T, int VEC, int LPN, int NIN>
 __global__ void __launch_bounds__(256, 4) mttkrp_kernel(const MttkrpParams p) {
     __shared__ __align__(16) WarpStage stage[8];
     const int lane = threadIdx.x & 31;
     WarpStage& st = stage[threadIdx.x >> 5];
-    const uint64_t pol = policy_evict_first();
     const int q = lane % LPN;
     const T* fl[NIN];  // this lane's first rank in every input factor
 #pragma unroll
     for (int n = 0; n < NIN; ++n) fl[n] = static_cast<const T*>(p.fac[n]) + q * VEC;
+    const int total = p.S + p.S_S;  // long segments first, then short segments
     int s = 0;
     if (lane == 0) s = atomicAdd(p.queue, 1);
     s = __shfl_sync(0xffffffffu, s, 0);
-    while (s < p.S) {
+    while (s < total) {
         int nxt = 0;
         if (lane == 0) nxt = atomicAdd(p.queue, 1);  // next ticket, latency hidden by this segment
-        mttkrp_segment<T, VEC, LPN, NIN>(p, s, st, lane, fl, pol);
+        if (s < p.S)
+            mttkrp_segment<T, VEC, LPN, NIN>(p, s, st, lane, fl);
+        else
+            mttkrp_short<T, VEC, LPN, NIN>(p, s - p.S, st, lane, fl);
         s = __shfl_sync(0xffffffffu, nxt, 0);
     }
 }
@@ -549,7 +604,7 @@ __global__ void __launch_bounds__(256, 4) mttkrp_kernel(const MttkrpParams p) {
 template <typename T, int VEC, int LPN, int NM>
 __global__ void __launch_bounds__(256) sample_kernel(const SampleParams p) {
     constexpr int NB = 4 * LPN;
-    constexpr int CH = Chunk<VEC>::value < NB ? Chunk<VEC>::value : NB;
+    constexpr int CH = 4;  // a multiple of 4: step u of a chunk is component u of its lane's int4
     const int lane = threadIdx.x & 31;
     const int q = lane % LPN;
     const unsigned wmask = (LPN == 32 ? 0xffffffffu : ((1u << LPN) - 1u)) << (lane - q);
@@ -579,7 +634,9 @@ __global__ void __launch_bounds__(256) sample_kernel(const SampleParams p) {
                     const int c = __shfl_sync(wmask, comp_rt(bi[n], u & 3), j >> 2, LPN);
                     float x[VEC];
                     if (active) {
-                        Row<T, VEC>::load(p.fac[n], (int64_t)c * p.R + rq, x);
+                        Raw<T, VEC> raw;
+                        raw.load(static_cast<const T*>(p.fac[n]) + (int64_t)c * p.R + rq);
+                        widen(raw, x);
                     } else {
 #pragma unroll
                         for (int e = 0; e < VEC; ++e) x[e] = 0.f;

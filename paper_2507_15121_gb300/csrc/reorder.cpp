@@ -158,14 +158,82 @@ bool order_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx
            sort_mode(nnz, nmodes, dims, idx, mode, threads, hm, pre.perm.p);
 }
 
+bool classify_rows(HostMode& hm, int threshold, int threads) {
+    const int64_t I = hm.I;
+    const int32_t* rp = hm.rowptr.p;
+    const int T = nthreads(threads);
+    const int64_t thr = threshold > 0 ? threshold : 1;
+    // count classes and short-row lengths (short lengths are < thr)
+    int64_t L = 0, nnz_L = 0;
+    std::vector<int64_t> cnt((size_t)thr, 0);
+    for (int64_t i = 0; i < I; ++i) {
+        const int64_t len = (int64_t)rp[i + 1] - rp[i];
+        if (len >= thr) {
+            ++L;
+            nnz_L += len;
+        } else {
+            ++cnt[(size_t)len];
+        }
+    }
+    const int64_t Sr = I - L;
+    hm.L = (int32_t)L;
+    hm.nnz_L = nnz_L;
+    hm.Sr = (int32_t)Sr;
+    if (!hm.rows_L.alloc((size_t)L) || !hm.rowptr_L.alloc((size_t)L + 1) || !hm.rows_S.alloc((size_t)Sr) ||
+        !hm.rowptr_S.alloc((size_t)Sr + 1))
+        return false;
+    // short rows by decreasing length, ties by increasing id (counting sort)
+    std::vector<int64_t> start((size_t)thr, 0);
+    int64_t run = 0;
+    for (int64_t len = thr - 1; len >= 0; --len) {
+        start[(size_t)len] = run;
+        run += cnt[(size_t)len];
+    }
+    int64_t jl = 0;
+    hm.rowptr_L[0] = 0;
+    for (int64_t i = 0; i < I; ++i) {
+        const int64_t len = (int64_t)rp[i + 1] - rp[i];
+        if (len >= thr) {
+            hm.rows_L[(size_t)jl] = (int32_t)i;
+            hm.rowptr_L[(size_t)jl + 1] = (int32_t)(hm.rowptr_L[(size_t)jl] + len);
+            ++jl;
+        } else {
+            hm.rows_S[(size_t)start[(size_t)len]++] = (int32_t)i;
+        }
+    }
+    hm.rowptr_S[0] = (int32_t)nnz_L;
+    for (int64_t j = 0; j < Sr; ++j) {
+        const int32_t r = hm.rows_S[(size_t)j];
+        hm.rowptr_S[(size_t)j + 1] = hm.rowptr_S[(size_t)j] + (rp[r + 1] - rp[r]);
+    }
+    // the copy's order: long rows, then short rows
+    HostBuf<int32_t> np;
+    if (!np.alloc((size_t)hm.nnz)) return false;
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(T)
+    for (int64_t j = 0; j < L; ++j) {
+        const int32_t r = hm.rows_L[(size_t)j];
+        std::memcpy(np.p + hm.rowptr_L[(size_t)j], hm.perm.p + rp[r], (size_t)(rp[r + 1] - rp[r]) * 4);
+    }
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(T)
+    for (int64_t j = 0; j < Sr; ++j) {
+        const int32_t r = hm.rows_S[(size_t)j];
+        if (rp[r + 1] > rp[r])
+            std::memcpy(np.p + hm.rowptr_S[(size_t)j], hm.perm.p + rp[r], (size_t)(rp[r + 1] - rp[r]) * 4);
+    }
+    std::swap(hm.perm.p, np.p);
+    std::swap(hm.perm.n, np.n);
+    return true;
+}
+
 bool cut_segments(HostMode& hm, int items) {
-    const int64_t I = hm.I, nnz = hm.nnz, total = I + nnz;
+    // ---- long part: merge path over the long rows
+    const int64_t I = hm.L, nnz = hm.nnz_L, total = I + nnz;
     const int64_t S = (total + items - 1) / items;
     hm.S = (int32_t)S;
     if (!hm.seg_row.alloc((size_t)S + 1) || !hm.seg_nz.alloc((size_t)S + 1)) return false;
-    const int32_t* rp = hm.rowptr.p;
-    // Boundary d = s*items on the merge path: the end of row i sits at position
-    // rowptr[i+1] + i; the rows completed before d are those whose end lies
+    const int32_t* rp = hm.rowptr_L.p;
+    // Boundary d = s*items on the merge path: the end of long row i sits at position
+    // rowptr_L[i+1] + i; the rows completed before d are those whose end lies
     // before d, found by binary search; the rest of d counts consumed nonzeros.
 #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s <= S; ++s) {
@@ -192,11 +260,12 @@ bool cut_segments(HostMode& hm, int items) {
     if (!hm.splits.alloc(sp.size())) return false;
     if (!sp.empty()) std::memcpy(hm.splits.p, sp.data(), sp.size() * sizeof(SplitRow));
     // combine tasks: the slots of split row j are T[s_a-1], H[s_a], ..., H[s_b],
-    // cut into runs of at most kCombineSlots consecutive segments
+    // cut into runs of at most kCombineSlots consecutive segments; split_info
+    // carries the output row id
     std::vector<int32_t> tasks, info, multi;
     for (int32_t j = 0; j < hm.nsplit; ++j) {
         const SplitRow& r = sp[(size_t)j];
-        info.push_back(r.row);
+        info.push_back(hm.rows_L[(size_t)r.row]);
         info.push_back((int32_t)(tasks.size() / 4));
         int32_t nt = 0;
         for (int32_t lo = r.s_a - 1; lo <= r.s_b; lo += kCombineSlots, ++nt) {
@@ -216,6 +285,21 @@ bool cut_segments(HostMode& hm, int items) {
     if (!tasks.empty()) std::memcpy(hm.tasks.p, tasks.data(), tasks.size() * 4);
     std::memcpy(hm.split_info.p, info.data(), info.size() * 4);
     if (!multi.empty()) std::memcpy(hm.multi.p, multi.data(), multi.size() * 4);
+
+    // ---- short part: greedy runs of short rows
+    std::vector<int32_t> ss;
+    int64_t j = 0;
+    while (j < hm.Sr) {
+        ss.push_back((int32_t)j);
+        const int64_t k0 = hm.rowptr_S[(size_t)j];
+        int64_t e = j;
+        while (e < hm.Sr && e - j < kShortRows && hm.rowptr_S[(size_t)e + 1] - k0 <= kShortNnz) ++e;
+        j = e;
+    }
+    ss.push_back((int32_t)hm.Sr);
+    hm.S_S = (int32_t)ss.size() - 1;
+    if (!hm.seg_short.alloc(ss.size())) return false;
+    std::memcpy(hm.seg_short.p, ss.data(), ss.size() * 4);
     return true;
 }
 

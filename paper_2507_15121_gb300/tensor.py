@@ -42,7 +42,8 @@ class Tensor:
     """
 
     def __init__(self, dims, idx, vals, *, segment_items: int = 0, keep_perm: bool = True, keep_coo: bool = True,
-                 max_rank: int = 0, host_threads: int = 0, inner_order: str = "lexicographic"):
+                 max_rank: int = 0, host_threads: int = 0, inner_order: str = "lexicographic",
+                 short_rows: int = 0):
         L = _lib.lib()
         self.dims = tuple(int(d) for d in dims)
         idx = np.ascontiguousarray(idx.numpy() if hasattr(idx, "numpy") else idx, dtype=np.int32)
@@ -54,7 +55,7 @@ class Tensor:
         if inner_order not in ("lexicographic", "stable"):
             raise ValueError("inner_order must be 'lexicographic' or 'stable'")
         opts = _lib.Opts(segment_items, 1 if keep_perm else 2, 1 if keep_coo else 2, max_rank, host_threads,
-                         2 if inner_order == "lexicographic" else 1)
+                         2 if inner_order == "lexicographic" else 1, short_rows)
         h = ctypes.c_void_p()
         _lib.check(L.amped_tensor_create(self.nnz, len(self.dims), dims_a.ctypes.data,
                                          idx.ctypes.data if self.nnz else None,
@@ -182,23 +183,32 @@ class Tensor:
                                                       stop.cuda_event if stop else None))
 
 
-def plan_mode(dims, idx, mode: int, segment_items: int = 0, inner_order: str = "lexicographic") -> dict:
-    """Host-only: the reorder and merge-path segment table for one mode."""
+def plan_mode(dims, idx, mode: int, segment_items: int = 0, inner_order: str = "lexicographic",
+              short_rows: int = 0) -> dict:
+    """Host-only: the reorder, row classes and segment tables for one mode."""
     L = _lib.lib()
     dims_a = np.asarray(dims, dtype=np.int64)
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     nnz = int(idx.shape[0])
-    I = int(dims_a[mode])
-    items = segment_items if segment_items > 0 else 1024
-    S = -(-(I + nnz) // items)
-    perm = np.empty(nnz, np.int32)
-    rowptr = np.empty(I + 1, np.int32)
-    seg_row = np.empty(S + 1, np.int32)
-    seg_nz = np.empty(S + 1, np.int32)
-    splits = np.empty((max(S, 1), 3), np.int32)
-    ns = ctypes.c_int32()
-    _lib.check(L.amped_plan_mode(nnz, len(dims_a), dims_a.ctypes.data, idx.ctypes.data if nnz else None, mode,
-                                 segment_items, 2 if inner_order == "lexicographic" else 1, perm.ctypes.data, rowptr.ctypes.data, seg_row.ctypes.data,
-                                 seg_nz.ctypes.data, splits.ctypes.data, ctypes.byref(ns)))
-    return {"perm": perm, "rowptr": rowptr, "seg_row": seg_row, "seg_nz": seg_nz, "splits": splits[: ns.value],
-            "items": items, "S": S}
+    io = 2 if inner_order == "lexicographic" else 1
+    args = (nnz, len(dims_a), dims_a.ctypes.data, idx.ctypes.data if nnz else None, mode, segment_items, io,
+            short_rows)
+    sz = _lib.PlanSizes()
+    _lib.check(L.amped_plan_mode(*args, ctypes.byref(sz), *([None] * 9)))
+    out = {
+        "perm": np.empty(nnz, np.int32),
+        "rows_long": np.empty(sz.long_rows, np.int32),
+        "rowptr_long": np.empty(sz.long_rows + 1, np.int32),
+        "seg_row": np.empty(sz.long_segments + 1, np.int32),
+        "seg_nz": np.empty(sz.long_segments + 1, np.int32),
+        "splits": np.empty((max(sz.split_rows, 1), 3), np.int32),
+        "rows_short": np.empty(sz.short_rows, np.int32),
+        "rowptr_short": np.empty(sz.short_rows + 1, np.int32),
+        "seg_short": np.empty(sz.short_segments + 1, np.int32),
+    }
+    ptrs = [a.ctypes.data if a.size else None for a in out.values()]
+    _lib.check(L.amped_plan_mode(*args, ctypes.byref(sz), *ptrs))
+    out["splits"] = out["splits"][: sz.split_rows]
+    out["sizes"] = {f: getattr(sz, f) for f, _ in _lib.PlanSizes._fields_}
+    out["items"] = segment_items if segment_items > 0 else 1024
+    return out

@@ -288,3 +288,23 @@ def test_zipf3_full_size_sampled_rows():
         counts = np.bincount(c.idx[:, m], minlength=c.dims[m])
         empty = np.flatnonzero(counts == 0)[:1000]
         assert np.all(outs[m][empty] == 0)
+
+
+@pytest.mark.slow
+def test_zipf4_billion_full_size_sampled_rows():
+    """50M x 20M x 5M x 1000, 1.0B nonzeros (modes 0-2 Zipf(1.2), mode 3 uniform,
+    lognormal values), R=32 fp32 factors: all-mode MTTKRP with the four mode copies
+    resident in HBM; 2048 seeded rows per mode (plus the 16 hottest) against the oracle."""
+    w = synth.WORKLOADS["zipf4"]
+    c = synth.make(w)
+    F = synth.factors(c.dims, 32, w.seed)
+    t = amped.Tensor(c.dims, c.idx, c.vals)
+    Fd = [dev(f) for f in F]
+    outs = [o.cpu().numpy() for o in t.mttkrp_all(Fd)]
+    del Fd
+    t.close()
+    torch.cuda.empty_cache()
+    for m in range(4):
+        rows = sampled_rows(c, m, 2048, w.seed)
+        ref = oracle.mttkrp_rows(c.dims, c.idx, c.vals, F, m, rows)
+        assert oracle.row_error(outs[m][rows], ref) <= FP32_BAR, m

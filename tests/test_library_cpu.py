@@ -68,34 +68,47 @@ def test_argument_errors_without_gpu(L):
     assert L.amped_tensor_destroy(None) == _lib.OK
 
 
-def check_plan(dims, idx, mode, items, inner_order="lexicographic"):
-    p = plan_mode(dims, idx, mode, items, inner_order)
+def check_plan(dims, idx, mode, items, inner_order="lexicographic", short_rows=0):
+    p = plan_mode(dims, idx, mode, items, inner_order, short_rows)
     nnz, I = idx.shape[0], dims[mode]
     keys = idx[:, mode]
     if inner_order == "stable":  # by the mode's coordinate, ties in caller order
-        np.testing.assert_array_equal(p["perm"], np.argsort(keys, kind="stable"))
+        base = np.argsort(keys, kind="stable")
     else:  # by (mode coordinate, coordinate of the largest other mode), ties in caller order
         others = [n for n in range(len(dims)) if n != mode]
         inner = max(others, key=lambda n: (dims[n], -n)) if others else None
-        order = np.lexsort((idx[:, inner], keys)) if inner is not None else np.argsort(keys, kind="stable")
-        np.testing.assert_array_equal(p["perm"], order)
-    np.testing.assert_array_equal(p["rowptr"], np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=I))]))
-    sr, sz, S = p["seg_row"].astype(np.int64), p["seg_nz"].astype(np.int64), p["S"]
-    total = I + nnz
+        base = np.lexsort((idx[:, inner], keys)) if inner is not None else np.argsort(keys, kind="stable")
+    lens = np.bincount(keys, minlength=I)
+    rp = np.concatenate([[0], np.cumsum(lens)])
+    thr = 32 if short_rows == 0 else (1 if short_rows < 0 else min(short_rows, 125))
+    long_rows = np.flatnonzero(lens >= thr)
+    short = np.flatnonzero(lens < thr)
+    short = short[np.lexsort((short, -lens[short]))]  # decreasing length, ties by id
+    np.testing.assert_array_equal(p["rows_long"], long_rows)
+    np.testing.assert_array_equal(p["rows_short"], short)
+    order = [base[rp[r]:rp[r + 1]] for r in long_rows] + [base[rp[r]:rp[r + 1]] for r in short]
+    exp_perm = np.concatenate(order) if order else np.zeros(0, np.int64)
+    np.testing.assert_array_equal(p["perm"], exp_perm)
+    nnz_L = int(lens[long_rows].sum())
+    np.testing.assert_array_equal(p["rowptr_long"], np.concatenate([[0], np.cumsum(lens[long_rows])]))
+    np.testing.assert_array_equal(p["rowptr_short"], nnz_L + np.concatenate([[0], np.cumsum(lens[short])]))
+    # long part: merge path over the long rows
+    L = len(long_rows)
+    sr, sz, S = p["seg_row"].astype(np.int64), p["seg_nz"].astype(np.int64), p["sizes"]["long_segments"]
+    total = L + nnz_L
+    assert S == -(-total // p["items"])
     d = np.minimum(np.arange(S + 1, dtype=np.int64) * p["items"], total)
     np.testing.assert_array_equal(sr + sz, d)
-    assert sr[0] == 0 and sz[0] == 0 and sr[-1] == I and sz[-1] == nnz
+    assert sr[0] == 0 and sz[0] == 0 and sr[-1] == L and sz[-1] == nnz_L
     assert np.all(np.diff(sr) >= 0) and np.all(np.diff(sz) >= 0)
-    rp = p["rowptr"].astype(np.int64)
-    # merge-path consistency: rows before seg_row are complete, the current row is partly consumed
-    for s in range(S + 1):
+    rpl = p["rowptr_long"].astype(np.int64)
+    for s in range(S + 1):  # rows before seg_row are complete, the current row is partly consumed
         r = sr[s]
-        if r < I:
-            assert rp[r] <= sz[s] <= rp[r + 1]
+        if r < L:
+            assert rpl[r] <= sz[s] <= rpl[r + 1]
         if r > 0:
-            assert rp[r] <= sz[s]
-    # split rows = rows straddling boundaries, grouped by row
-    straddled = [(int(sr[s]), s) for s in range(1, S) if sr[s] < I and sz[s] > rp[sr[s]]]
+            assert rpl[r] <= sz[s]
+    straddled = [(int(sr[s]), s) for s in range(1, S) if sr[s] < L and sz[s] > rpl[sr[s]]]
     exp = []
     for r, s in straddled:
         if exp and exp[-1][0] == r and exp[-1][2] == s - 1:
@@ -103,23 +116,36 @@ def check_plan(dims, idx, mode, items, inner_order="lexicographic"):
         else:
             exp.append([r, s, s])
     np.testing.assert_array_equal(p["splits"].reshape(-1, 3), np.array(exp, dtype=np.int32).reshape(-1, 3))
+    # short part: greedy segments of at most 31 rows and 124 nonzeros covering every short row
+    ss = p["seg_short"].astype(np.int64)
+    rps = p["rowptr_short"].astype(np.int64)
+    assert ss[0] == 0 and ss[-1] == len(short) and np.all(np.diff(ss) > 0) or len(short) == 0
+    for t in range(len(ss) - 1):
+        a, b = ss[t], ss[t + 1]
+        assert b - a <= 31 and rps[b] - rps[a] <= 124
+        if b < len(short):  # greedy: the next row would not have fitted
+            assert b - a == 31 or rps[b + 1] - rps[a] > 124
     return p
 
 
 def simulate_kernel(p, dims, idx, vals, F, mode):
-    """The MTTKRP kernel's per-segment walk and flush rules, then the
-    deterministic combine of split rows, in plain Python (fp64)."""
+    """The MTTKRP kernel in plain Python (fp64): long segments walk their rows
+    with the flush rules (complete rows stored, head/tail partials of split
+    rows), short segments store their rows whole, then the split rows are
+    combined in segment order."""
     I = dims[mode]
     R = F[0].shape[1]
-    perm, rp = p["perm"], p["rowptr"].astype(np.int64)
+    perm = p["perm"]
     contrib = vals[perm].astype(np.float64)[:, None] * np.ones((1, R))
     for n in range(len(dims)):
         if n != mode:
             contrib = contrib * F[n][idx[perm, n]].astype(np.float64)
     out = np.full((I, R), np.nan)
+    rows_L, rp = p["rows_long"], p["rowptr_long"].astype(np.int64)
+    L = len(rows_L)
     H, T = {}, {}
     sr, sz = p["seg_row"], p["seg_nz"]
-    for s in range(p["S"]):
+    for s in range(p["sizes"]["long_segments"]):
         row_s, nz_s, row_e, nz_e = int(sr[s]), int(sz[s]), int(sr[s + 1]), int(sz[s + 1])
         cont = rp[row_s] < nz_s
         st = {"i": row_s, "acc": np.zeros(R), "touched": False}
@@ -132,8 +158,8 @@ def simulate_kernel(p, dims, idx, vals, F, mode):
                 assert s not in H
                 H[s] = st["acc"].copy()
             elif row < row_e:
-                assert np.isnan(out[row, 0]), "row written twice"
-                out[row] = st["acc"]
+                assert np.isnan(out[rows_L[row], 0]), "row written twice"
+                out[rows_L[row]] = st["acc"]
             else:
                 assert s not in T
                 T[s] = st["acc"].copy()
@@ -149,11 +175,16 @@ def simulate_kernel(p, dims, idx, vals, F, mode):
         while st["i"] < row_e:
             flush(st["i"])
             st["i"] += 1
-        if st["i"] < I and st["touched"]:
+        if st["i"] < L and st["touched"]:
             flush(st["i"])
+    rows_S, rps, ss = p["rows_short"], p["rowptr_short"].astype(np.int64), p["seg_short"]
+    for t in range(p["sizes"]["short_segments"]):
+        for j in range(int(ss[t]), int(ss[t + 1])):
+            assert np.isnan(out[rows_S[j], 0]), "row written twice"
+            out[rows_S[j]] = contrib[rps[j]:rps[j + 1]].sum(axis=0)
     for row, s_a, s_b in p["splits"]:
-        assert np.isnan(out[row, 0])
-        out[row] = T[s_a - 1] + sum(H[s] for s in range(s_a, s_b + 1))
+        assert np.isnan(out[rows_L[row], 0])
+        out[rows_L[row]] = T[s_a - 1] + sum(H[s] for s in range(s_a, s_b + 1))
     assert not np.any(np.isnan(out)), "a row was never written"
     return out
 
@@ -178,12 +209,13 @@ def make_case(name, dims, nnz, seed):
 
 @pytest.mark.parametrize("name,dims,nnz,seed", CASES)
 @pytest.mark.parametrize("items", [1, 7, 32, 1024, 10 ** 6])
-@pytest.mark.parametrize("inner_order", ["lexicographic", "stable"])
-def test_plan_and_simulated_kernel_match_oracle(name, dims, nnz, seed, items, inner_order):
+@pytest.mark.parametrize("inner_order,short_rows", [("lexicographic", 0), ("stable", 0), ("lexicographic", -1),
+                                                    ("stable", 5), ("lexicographic", 200)])
+def test_plan_and_simulated_kernel_match_oracle(name, dims, nnz, seed, items, inner_order, short_rows):
     idx, vals = make_case(name, dims, nnz, seed)
     F = [np.random.default_rng(seed + n).uniform(0, 1, (d, 3)).astype(np.float32) for n, d in enumerate(dims)]
     for mode in range(len(dims)):
-        p = check_plan(dims, idx, mode, items, inner_order)
+        p = check_plan(dims, idx, mode, items, inner_order, short_rows)
         got = simulate_kernel(p, dims, idx, vals, F, mode)
         np.testing.assert_allclose(got, oracle.mttkrp(dims, idx, vals, F, mode), rtol=1e-12, atol=1e-12)
 
@@ -191,7 +223,7 @@ def test_plan_and_simulated_kernel_match_oracle(name, dims, nnz, seed, items, in
 def test_plan_empty_tensor_and_zipf():
     dims = (10, 4, 3)
     p = check_plan(dims, np.zeros((0, 3), np.int32), 0, 4)
-    assert p["S"] == 3 and len(p["splits"]) == 0
+    assert p["sizes"]["long_segments"] == 0 and p["sizes"]["short_rows"] == 10 and len(p["splits"]) == 0
     w = synth.WORKLOADS["zipf3"].scaled(0.0002)
     c = synth.make(w)
     for mode in range(3):
