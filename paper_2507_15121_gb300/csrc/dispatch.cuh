@@ -10,6 +10,8 @@
 
 namespace amped {
 
+constexpr int kCarveoutPercent = 30;  // ~68 KB of the 228 KB shared-memory maximum: 4 blocks x 16 KB
+
 template <typename K>
 static int blocks_per_sm(K kernel) {
     int nb = 0;
@@ -42,7 +44,13 @@ template <typename T, int VEC, int LPN, int NIN>
 static int launch_mttkrp_shape(const MttkrpParams& p, int grid_cap, cudaStream_t st) {
     auto k = mttkrp_kernel<T, VEC, LPN, NIN>;
     static int grid = 0;  // persistent grid: every resident block slot on every SM
-    if (grid == 0) grid = blocks_per_sm(k) * device_sms();
+    if (grid == 0) {
+        // The kernel needs little shared memory (the staged stream batches);
+        // ask for the smallest carveout so the rest of the SM's 256 KB stays L1
+        // cache for the factor-row gathers.
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, kCarveoutPercent);
+        grid = blocks_per_sm(k) * device_sms();
+    }
     int g = grid;
     if (grid_cap > 0 && g > grid_cap) g = grid_cap;
     k<<<g, 256, 0, st>>>(p);
