@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--short-rows", type=int, default=0, help="short-row threshold (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the 16-bit factor variants")
+    ap.add_argument("--lowp", default="", help="16-bit factor variants to time, e.g. bf16,f16 "
+                                              "(default: bf16; bf16,f16 for zipf3_r64)")
     return ap.parse_args()
 
 
@@ -186,11 +188,19 @@ def recorded_traffic(workload: str):
         return None
 
 
+def kernel_name(dtype: str, R: int, N: int) -> str:
+    vec = 8 if dtype == "float" else 16
+    lpn = 2
+    while lpn * vec < R:
+        lpn *= 2
+    return f"mttkrp_kernel<{dtype},{vec},{lpn},{N - 1}>"
+
+
 def workload_config(w, args):
     return {"workload": w.name, "dims": list(w.dims), "nnz": w.nnz, "modes": len(w.dims), "rank": w.rank,
             "index_dist": [list(d) for d in w.index_dist], "values": list(w.values), "seed": w.seed,
             "factors": "fp32 U(0,1); bf16 variant rounded from the same draws",
-            "segment_items": args.segment_items or 1024, "inner_order": args.inner_order,
+            "segment_items": args.segment_items or "default", "inner_order": args.inner_order,
             "short_rows": args.short_rows or 32,
             "l2": "inputs_exceed_l2 (no flush)",
             "parallelism": "single GPU per rank; ranks run independent replicas"}
@@ -279,22 +289,27 @@ def run_ours(args, w, world, rank, local, pg):
     Fd = [torch.from_numpy(f).to(device) for f in F]
     peak, peak_kind = peaks()
 
+    lowp = [] if args.no_bf16 else [x for x in (args.lowp or ("bf16,f16" if w.name.startswith("zipf3_r64") else
+                                                            "bf16")).split(",") if x and x != "none"]
+    tdt = {"bf16": torch.bfloat16, "f16": torch.float16}
     barrier(pg, device)
     with ClockSampler(local) as clk:
         total, per_mode, launches = time_steps(t, Fd, K, W, torch, stream)
-        if not args.no_bf16:
-            Fb = [f.to(torch.bfloat16) for f in Fd]
-            total_b, per_mode_b, launches_b = time_steps(t, Fb, K, W, torch, stream)
+        lowp_res = {}
+        for name in lowp:
+            Fl = [f.to(tdt[name]) for f in Fd]
+            lowp_res[name] = time_steps(t, Fl, K, W, torch, stream)
+            del Fl
     barrier(pg, device)
     total = max_over_ranks(total, pg, device)
 
     B = bytes_model(c, w.rank, 4, U)
     kern_ms = [statistics.mean(x) for x in per_mode]
     achieved = sum(B) / (sum(kern_ms) * 1e-3) / 1e9
-    traffic = recorded_traffic(w.name)
+    traffic = recorded_traffic(w.name) if w.rank == 32 and args.scale == 1.0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind + " (STREAM-style copy, MEASURED_PEAKS.json)",
-            "kernel": "mttkrp_kernel<float,4,8,2>", "algorithmic_bytes_per_mode": B,
+            "kernel": kernel_name("float", w.rank, c.nmodes), "algorithmic_bytes_per_mode": B,
             "kernel_ms_per_mode": kern_ms}
     value = world * c.nnz * K / (total * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -303,18 +318,20 @@ def run_ours(args, w, world, rank, local, pg):
             "config": workload_config(w, args), "roofline": roof, "gpu_launches": launches,
             "clocks": getattr(clk, "result", None),
             "preprocess_s": {"generate": gen_s, "create": create_s}}
-    if not args.no_bf16:
-        Bb = bytes_model(c, w.rank, 2, U)
-        kb = [statistics.mean(x) for x in per_mode_b]
-        ach_b = sum(Bb) / (sum(kb) * 1e-3) / 1e9
-        total_b = max_over_ranks(total_b, pg, device)
-        line["variants"] = {"bf16_factors": {
-            "value": world * c.nnz * K / (total_b * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": total_b / K,
-            "gpu_launches": launches_b,
-            "roofline": {"bound": "hbm", "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
-                         "traffic": None, "kernel": "mttkrp_kernel<bf16,8,4,2>", "algorithmic_bytes_per_mode": Bb,
-                         "kernel_ms_per_mode": kb}}}
-        del Fb
+    if lowp_res:
+        line["variants"] = {}
+        Bl = bytes_model(c, w.rank, 2, U)
+    for name, (tot_l, per_l, launches_l) in lowp_res.items():
+        kl = [statistics.mean(x) for x in per_l]
+        ach_l = sum(Bl) / (sum(kl) * 1e-3) / 1e9
+        tot_l = max_over_ranks(tot_l, pg, device)
+        line["variants"][f"{name}_factors"] = {
+            "value": world * c.nnz * K / (tot_l * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": tot_l / K,
+            "gpu_launches": launches_l,
+            "roofline": {"bound": "hbm", "achieved": ach_l, "peak": peak, "unit": "GB/s", "frac": ach_l / peak,
+                         "traffic": None, "kernel": kernel_name("__nv_bfloat16" if name == "bf16" else "__half",
+                                                                w.rank, c.nmodes),
+                         "algorithmic_bytes_per_mode": Bl, "kernel_ms_per_mode": kl}}
 
     # end to end through the host-buffer entry point: factors in, outputs out, every step
     if not args.no_e2e:
@@ -354,12 +371,69 @@ def run_ours(args, w, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def run_completion(args, w, world, rank, local, pg):
+    """Gradient-based CP completion step on the planted tensor: forward = sampled
+    CP model at every nonzero, loss 1/2 sum (m - x)^2, backward = one MTTKRP per
+    mode with the residuals as values (autograd through CPSampled)."""
+    import torch
+    import paper_2507_15121_gb300 as amped
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    K, W = args.steps, args.warmup
+    t0 = time.time()
+    c = synth.make(w)
+    gen_s = time.time() - t0
+    t0 = time.time()
+    t = amped.Tensor(c.dims, c.idx, c.vals, segment_items=args.segment_items, inner_order=args.inner_order,
+                     short_rows=args.short_rows)
+    create_s = time.time() - t0
+    # observed entries: the planted rank-16 model at the coordinates plus the drawn noise
+    B = [torch.from_numpy(b).to(device) for b in c.extra["planted_factors"]]
+    x = t.cp_sample(B) + torch.from_numpy(c.extra["noise"]).to(device)
+    del B
+    A = [torch.from_numpy(a).to(device).requires_grad_(True)
+         for a in synth.factors(c.dims, w.rank, w.seed, scale=w.factor_scale)]
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        for a in A:
+            a.grad = None
+        amped.completion_loss(t, A, x).backward()
+    torch.cuda.synchronize()
+    barrier(pg, device)
+    l0 = amped.kernel_launches()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(K):
+            for a in A:
+                a.grad = None
+            loss = amped.completion_loss(t, A, x)
+            loss.backward()
+        stop.record(stream)
+        torch.cuda.synchronize()
+    total = max_over_ranks(start.elapsed_time(stop), pg, device)
+    launches = amped.kernel_launches() - l0
+    line = {"metric": "CP completion step (sampled model + MTTKRP gradient, autograd) Gnnz/s", "value":
+            world * c.nnz * K / (total * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic planted rank-16 CP tensor plus N(0, 0.01^2) noise at Zipf positions",
+            "config": workload_config(w, args), "roofline": None, "gpu_launches": launches,
+            "loss_last": float(loss.item()), "clocks": getattr(clk, "result", None),
+            "preprocess_s": {"generate": gen_s, "create": create_s}}
+    t.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     w = synth.WORKLOADS[args.workload].scaled(args.scale)
     world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, w, world, rank, pg)
+    elif w.planted_rank:
+        run_completion(args, w, world, rank, local, pg)
     else:
         run_ours(args, w, world, rank, local, pg)
     if pg is not None:

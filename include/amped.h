@@ -53,7 +53,8 @@ typedef enum { AMPED_F32 = 0, AMPED_BF16 = 1, AMPED_F16 = 2 } amped_dtype;
 /* Options for amped_tensor_create.  Zero-initialise and set what you need;
  * a field left at 0 takes its default. */
 typedef struct {
-    int32_t segment_items; /* work items (nonzeros + output rows) per segment; default 1024 */
+    int32_t segment_items; /* work items (nonzeros + output rows) per long-row segment; default:
+                              (nnz + rows) / (8 x resident warps), clamped to 256..4096 */
     int32_t keep_perm;     /* 1 = keep each copy's nonzero permutation on the device (needed by
                               amped_cp_grad); 2 = do not keep it; 0 = default (keep) */
     int32_t keep_coo;      /* 1 = keep the coordinates in caller order on the device (needed by
@@ -159,7 +160,7 @@ typedef struct {
 /*
  * Host-only planning query: the reorder, row classes and segment tables that amped_tensor_create
  * builds for mode `mode`, without touching the GPU (for inspection and tests).  segment_items,
- * inner_order and short_rows as in amped_opts (0 = defaults).  Call once with every array NULL to
+ * inner_order and short_rows as in amped_opts (0 = defaults, except segment_items 0 = 1024 here).  Call once with every array NULL to
  * read `sizes`, then again with buffers of these lengths (any may be NULL to skip it):
  *   perm          [nnz]               caller index of the k-th nonzero of the mode's copy
  *   rows_long     [long_rows]         row ids of the long rows (increasing)

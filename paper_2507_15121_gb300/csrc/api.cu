@@ -179,6 +179,19 @@ amped_status ensure_scratch(amped_tensor* t, int R) {
     return AMPED_OK;
 }
 
+// Default segment size: large segments (fewer split rows, fewer tickets) but at
+// least ~8 segments per resident warp of the persistent grid, so the ticket
+// queue can still balance the load.
+int default_segment_items(int64_t nnz, int nmodes, const int64_t* dims, int device) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) sms = 152;
+    int64_t rows = 0;
+    for (int n = 0; n < nmodes; ++n) rows = std::max<int64_t>(rows, dims[n]);
+    const int64_t warps = (int64_t)sms * 32;  // 4 blocks of 8 warps per SM
+    const int64_t per = (nnz + rows) / (8 * warps);
+    return (int)std::min<int64_t>(4096, std::max<int64_t>(256, per));
+}
+
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 amped_status check_call(amped_tensor* t, const void* const* factors, amped_dtype fdtype, int R, int skip_mode,
@@ -293,7 +306,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         if (dims[n] < 1 || dims[n] > (int64_t)INT32_MAX - 4 * kPad)
             return fail(AMPED_ERR_INVALID, "dims[%d]=%lld outside 1..2^31-%d", n, (long long)dims[n], 4 * kPad);
     if (nnz > 0 && (!idx || !vals)) return fail(AMPED_ERR_INVALID, "idx or vals is NULL");
-    int items = 1024, threads = 0, max_rank = 64, short_thr = 32;
+    int items = 0, threads = 0, max_rank = 64, short_thr = 32;
     bool keep_perm = true, keep_coo = true, inner_sort = true;
     if (opts) {
         if (opts->segment_items < 0 || opts->max_rank < 0 || opts->host_threads < 0)
@@ -317,6 +330,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
     amped_tensor* t = new (std::nothrow) amped_tensor;
     if (!t) return fail(AMPED_ERR_OOM, "host allocation failed");
     cudaGetDevice(&t->device);
+    if (items == 0) items = default_segment_items(nnz, nmodes, dims, t->device);
     t->N = nmodes;
     t->nnz = nnz;
     for (int n = 0; n < nmodes; ++n) t->dims[n] = dims[n];
@@ -568,7 +582,7 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
         if (dims[n] < 1 || dims[n] > (int64_t)INT32_MAX - 4 * kPad)
             return fail(AMPED_ERR_INVALID, "dims[%d]=%lld out of range", n, (long long)dims[n]);
     if (nnz > 0 && !idx) return fail(AMPED_ERR_INVALID, "idx is NULL");
-    const int items = segment_items > 0 ? segment_items : 1024;
+    const int items = segment_items > 0 ? segment_items : 1024;  // host-only query: no device to size for
     const int thr = short_rows > 0 ? std::min(short_rows, kShortNnz + 1) : short_rows < 0 ? 1 : 32;
     const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, 0);
     if (bad >= 0) return fail(AMPED_ERR_INDEX, "nonzero %lld has a coordinate outside dims", (long long)bad);
