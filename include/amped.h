@@ -109,8 +109,8 @@ amped_status amped_tensor_info(amped_tensor_t t, int64_t* nnz, int* nmodes, int6
  *   out(i, r) = sum over nonzeros x with i_mode = i of val(x) * prod_{n != mode} A_n(i_n, r)
  *   factors  host array of N device pointers; factors[n] is [dims[n]][R] in `fdtype`;
  *            factors[mode] is not read and may be NULL
- *   R        rank, 1..128 for fp32 and 1..256 for bf16/fp16 (R > 32 needs R % 4 == 0 for fp32,
- *            R % 8 == 0 for 16-bit)
+ *   R        rank, 1..256 for fp32 and 1..512 for bf16/fp16 (R > 32 needs R % 8 == 0 for fp32,
+ *            R % 16 == 0 for 16-bit); tensors of 2 to 5 modes
  *   out      device [dims[mode]][R] fp32, fully overwritten (rows without nonzeros become 0)
  * Enqueues a scratch reset, the persistent MTTKRP kernel and the split-row combine on `stream`.
  */
@@ -148,6 +148,19 @@ amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped
  */
 amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
                            const float* gvals, float* const* grads, void* stream);
+
+/*
+ * Fused gradient of the CP completion loss over the tensor's own values x (the values given to
+ * amped_tensor_create), without materialising the sampled model or the residuals:
+ *   r_k = m_k - x_k,  m_k = sum_r prod_n A_n(i_n(k), r)          (CP model, paper Sec. 2.1)
+ *   grads[n](i, r) = sum_{k: i_n(k) = i} r_k * prod_{w != n} A_w(i_w(k), r)   (Sec. 3 EC with r_k)
+ *   *loss = 1/2 sum_k r_k^2                                      (fp64, device; may be NULL)
+ * One pass per mode over that mode's copy: each nonzero's model value is rebuilt from the
+ * output mode's factor row and the gathered Khatri-Rao row.  grads: host array of N device
+ * pointers [dims[n]][R] fp32, overwritten.  Equal to amped_cp_grad with gvals = m - x.
+ */
+amped_status amped_cp_completion_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
+                                      float* const* grads, double* loss, void* stream);
 
 /* Sizes of a mode's plan (amped_plan_mode). */
 typedef struct {

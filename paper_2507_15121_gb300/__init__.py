@@ -14,6 +14,7 @@ from ._lib import AmpedError, kernel_launches, version  # noqa: F401
 from .tensor import Tensor, plan_mode  # noqa: F401
 
 try:
-    from .autograd import CPSampled, completion_loss, sampled_model  # noqa: F401
+    from .autograd import (CPCompletionLoss, CPSampled, completion_loss, fused_completion_loss,  # noqa: F401
+                           sampled_model)
 except ImportError:  # torch missing: only the host planning query is usable
     pass

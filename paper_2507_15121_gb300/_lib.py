@@ -60,6 +60,7 @@ def lib() -> ctypes.CDLL:
             "amped_mttkrp_all_host": ([vp, vp, c_int, c_int, vp, vp], st),
             "amped_cp_sample": ([vp, vp, c_int, c_int, vp, vp], st),
             "amped_cp_grad": ([vp, vp, c_int, c_int, vp, vp, vp], st),
+            "amped_cp_completion_grad": ([vp, vp, c_int, c_int, vp, vp, vp], st),
             "amped_plan_mode": ([i64, c_int, vp, vp, c_int, c_int, c_int, c_int, ctypes.POINTER(PlanSizes)]
                                 + [vp] * 9, st),
             "amped_set_kernel_events": ([vp, vp, vp], st),

@@ -29,6 +29,33 @@ class CPSampled(torch.autograd.Function):
         return (None, *[g if need else None for g, need in zip(grads, needs)])
 
 
+class CPCompletionLoss(torch.autograd.Function):
+    """L = 1/2 sum_k (m_k - x_k)^2 over the tensor's own values, as one fused
+    pass per mode: the forward computes the loss and every factor gradient
+    together (amped_cp_completion_grad); the backward scales the stored
+    gradients by the incoming gradient of L."""
+
+    @staticmethod
+    def forward(ctx, tensor: Tensor, *factors):
+        grads, loss = tensor.completion_grad(list(factors))
+        ctx.save_for_backward(*grads)
+        ctx.dtypes = [f.dtype for f in factors]
+        return loss
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        grads = ctx.saved_tensors
+        out = [(g * grad_loss).to(dt) for g, dt in zip(grads, ctx.dtypes)]
+        needs = ctx.needs_input_grad[1:]
+        return (None, *[g if need else None for g, need in zip(out, needs)])
+
+
+def fused_completion_loss(tensor: Tensor, factors):
+    """1/2 sum_k (m_k - x_k)^2 over the tensor's stored values x, differentiable in
+    the factors, computed by the fused kernels (one pass per mode)."""
+    return CPCompletionLoss.apply(tensor, *factors)
+
+
 def sampled_model(tensor: Tensor, factors):
     """m_k at every nonzero (caller order), differentiable in the factors."""
     return CPSampled.apply(tensor, *factors)

@@ -124,6 +124,8 @@ struct MttkrpParams {
     float* out;                  // [I][R]
     float* part;                 // [S][2][R] head/tail partials of split rows
     int* queue;                  // segment ticket counter, zero at launch
+    const void* fout;            // residual mode: the output mode's factor [rows][R]
+    double* loss;                // residual mode: accumulates 1/2 sum (m - x)^2 (may be null)
     int32_t I, S, R, nnz;        // I: long rows; S: long segments
     int32_t S_S;                 // short segments (tickets S .. S+S_S-1)
 };

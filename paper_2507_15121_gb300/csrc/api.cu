@@ -20,6 +20,9 @@ namespace amped {
 int launch_mttkrp_f32(int nin, const MttkrpParams& p, int grid_cap, void* st);
 int launch_mttkrp_bf16(int nin, const MttkrpParams& p, int grid_cap, void* st);
 int launch_mttkrp_f16(int nin, const MttkrpParams& p, int grid_cap, void* st);
+int launch_residual_f32(int nin, const MttkrpParams& p, int grid_cap, void* st);
+int launch_residual_bf16(int nin, const MttkrpParams& p, int grid_cap, void* st);
+int launch_residual_f16(int nin, const MttkrpParams& p, int grid_cap, void* st);
 int launch_sample_f32(const SampleParams& p, void* st);
 int launch_sample_bf16(const SampleParams& p, void* st);
 int launch_sample_f16(const SampleParams& p, void* st);
@@ -212,14 +215,14 @@ amped_status check_call(amped_tensor* t, const void* const* factors, amped_dtype
         if (!aligned(factors[n], al)) return fail(AMPED_ERR_INVALID, "factor %d is not %zu-byte aligned", n, al);
     }
     if (t->N < 2 && skip_mode >= 0) return AMPED_OK;
-    if (t->N - 1 > 3 && skip_mode >= 0)
-        return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 4 modes, tensor has %d", t->N);
+    if (t->N - 1 > 4 && skip_mode >= 0)
+        return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 5 modes, tensor has %d", t->N);
     return AMPED_OK;
 }
 
 // One mode: reset the ticket counter, run the persistent kernel, combine split rows.
 amped_status run_mode(amped_tensor* t, int mode, const void* const* factors, amped_dtype fdtype, int R, int vec,
-                      float* out, const float* gval, cudaStream_t st) {
+                      float* out, const float* gval, cudaStream_t st, bool residual = false, double* loss = nullptr) {
     const DevMode& dm = t->m[mode];
     if (!out) return fail(AMPED_ERR_INVALID, "output for mode %d is NULL", mode);
     if (!aligned(out, vec > 1 ? 16 : 4)) return fail(AMPED_ERR_INVALID, "output for mode %d is misaligned", mode);
@@ -254,12 +257,22 @@ amped_status run_mode(amped_tensor* t, int mode, const void* const* factors, amp
     p.S = dm.S;
     p.R = R;
     p.nnz = (int32_t)t->nnz;
+    p.fout = residual ? factors[mode] : nullptr;
+    p.loss = residual ? loss : nullptr;
     if (t->ev_start) cudaEventRecord(static_cast<cudaEvent_t>(t->ev_start), st);
     int rc;
-    switch (fdtype) {
-        case AMPED_F32: rc = launch_mttkrp_f32(nin, p, 0, st); break;
-        case AMPED_BF16: rc = launch_mttkrp_bf16(nin, p, 0, st); break;
-        default: rc = launch_mttkrp_f16(nin, p, 0, st); break;
+    if (residual) {
+        switch (fdtype) {
+            case AMPED_F32: rc = launch_residual_f32(nin, p, 0, st); break;
+            case AMPED_BF16: rc = launch_residual_bf16(nin, p, 0, st); break;
+            default: rc = launch_residual_f16(nin, p, 0, st); break;
+        }
+    } else {
+        switch (fdtype) {
+            case AMPED_F32: rc = launch_mttkrp_f32(nin, p, 0, st); break;
+            case AMPED_BF16: rc = launch_mttkrp_bf16(nin, p, 0, st); break;
+            default: rc = launch_mttkrp_f16(nin, p, 0, st); break;
+        }
     }
     if (t->ev_stop) cudaEventRecord(static_cast<cudaEvent_t>(t->ev_stop), st);
     t->ev_start = t->ev_stop = nullptr;
@@ -453,7 +466,7 @@ amped_status amped_mttkrp_all(amped_tensor_t t, const void* const* factors, ampe
     int vec = 0;
     amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
     if (s != AMPED_OK) return s;
-    if (t->N - 1 > 3) return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 4 modes");
+    if (t->N - 1 > 4) return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 5 modes");
     for (int n = 0; n < t->N; ++n)
         if (!outs[n]) return fail(AMPED_ERR_INVALID, "output for mode %d is NULL", n);
     for (int n = 0; n < t->N; ++n) {
@@ -524,7 +537,7 @@ amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped
     int vec = 0;
     amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
     if (s != AMPED_OK) return s;
-    if (t->N < 2 || t->N > 4) return fail(AMPED_ERR_UNSUPPORTED, "sampled-model kernels are built for 2 to 4 modes");
+    if (t->N < 2 || t->N > 5) return fail(AMPED_ERR_UNSUPPORTED, "sampled-model kernels are built for 2 to 5 modes");
     if (t->nnz == 0) return AMPED_OK;
     if (!m_out || !aligned(m_out, 16)) return fail(AMPED_ERR_INVALID, "m_out is NULL or not 16-byte aligned");
     SampleParams p{};
@@ -558,7 +571,7 @@ amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_d
     int vec = 0;
     amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
     if (s != AMPED_OK) return s;
-    if (t->N - 1 > 3) return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 4 modes");
+    if (t->N - 1 > 4) return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 5 modes");
     for (int n = 0; n < t->N; ++n)
         if (!grads[n]) return fail(AMPED_ERR_INVALID, "gradient %d is NULL", n);
     for (int n = 0; n < t->N; ++n) {
@@ -614,6 +627,30 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
     if (rows_short && hm.Sr) std::memcpy(rows_short, hm.rows_S.p, (size_t)hm.Sr * 4);
     if (rowptr_short) std::memcpy(rowptr_short, hm.rowptr_S.p, ((size_t)hm.Sr + 1) * 4);
     if (seg_short) std::memcpy(seg_short, hm.seg_short.p, ((size_t)hm.S_S + 1) * 4);
+    return AMPED_OK;
+}
+
+amped_status amped_cp_completion_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
+                                      float* const* grads, double* loss, void* stream) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (!grads) return fail(AMPED_ERR_INVALID, "gradient pointer array is NULL");
+    int vec = 0;
+    amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
+    if (s != AMPED_OK) return s;
+    if (t->N < 2 || t->N - 1 > 4) return fail(AMPED_ERR_UNSUPPORTED, "completion kernels are built for 2 to 5 modes");
+    for (int n = 0; n < t->N; ++n)
+        if (!grads[n]) return fail(AMPED_ERR_INVALID, "gradient %d is NULL", n);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (loss) {
+        cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), st);
+        if (e != cudaSuccess) return cuda_fail(e, "loss reset");
+    }
+    for (int n = 0; n < t->N; ++n) {
+        // the loss is accumulated once, in the pass over mode 0
+        s = run_mode(t, n, factors, fdtype, R, vec, grads[n], nullptr, st, true, n == 0 ? loss : nullptr);
+        if (s != AMPED_OK) return s;
+    }
     return AMPED_OK;
 }
 

@@ -40,9 +40,9 @@ struct Shape {
     }
 };
 
-template <typename T, int VEC, int LPN, int NIN>
+template <typename T, int VEC, int LPN, int NIN, bool RES>
 static int launch_mttkrp_shape(const MttkrpParams& p, int grid_cap, cudaStream_t st) {
-    auto k = mttkrp_kernel<T, VEC, LPN, NIN>;
+    auto k = mttkrp_kernel<T, VEC, LPN, NIN, RES>;
     static int grid = 0;  // persistent grid: every resident block slot on every SM
     if (grid == 0) {
         // The kernel needs little shared memory (the staged stream batches);
@@ -57,37 +57,38 @@ static int launch_mttkrp_shape(const MttkrpParams& p, int grid_cap, cudaStream_t
     return (int)cudaGetLastError();
 }
 
-template <typename T, int VEC, int NIN>
+template <typename T, int VEC, int NIN, bool RES>
 static int launch_mttkrp_lpn(int lpn, const MttkrpParams& p, int grid_cap, cudaStream_t st) {
     if constexpr (VEC == 1) {
-        return launch_mttkrp_shape<T, 1, 32, NIN>(p, grid_cap, st);
+        return launch_mttkrp_shape<T, 1, 32, NIN, RES>(p, grid_cap, st);
     } else {
         switch (lpn) {
-            case 2: return launch_mttkrp_shape<T, VEC, 2, NIN>(p, grid_cap, st);
-            case 4: return launch_mttkrp_shape<T, VEC, 4, NIN>(p, grid_cap, st);
-            case 8: return launch_mttkrp_shape<T, VEC, 8, NIN>(p, grid_cap, st);
-            case 16: return launch_mttkrp_shape<T, VEC, 16, NIN>(p, grid_cap, st);
-            default: return launch_mttkrp_shape<T, VEC, 32, NIN>(p, grid_cap, st);
+            case 2: return launch_mttkrp_shape<T, VEC, 2, NIN, RES>(p, grid_cap, st);
+            case 4: return launch_mttkrp_shape<T, VEC, 4, NIN, RES>(p, grid_cap, st);
+            case 8: return launch_mttkrp_shape<T, VEC, 8, NIN, RES>(p, grid_cap, st);
+            case 16: return launch_mttkrp_shape<T, VEC, 16, NIN, RES>(p, grid_cap, st);
+            default: return launch_mttkrp_shape<T, VEC, 32, NIN, RES>(p, grid_cap, st);
         }
     }
 }
 
-template <typename T, int VEC>
+template <typename T, int VEC, bool RES>
 static int launch_mttkrp_nin(int nin, int lpn, const MttkrpParams& p, int grid_cap, cudaStream_t st) {
     switch (nin) {
-        case 1: return launch_mttkrp_lpn<T, VEC, 1>(lpn, p, grid_cap, st);
-        case 2: return launch_mttkrp_lpn<T, VEC, 2>(lpn, p, grid_cap, st);
-        case 3: return launch_mttkrp_lpn<T, VEC, 3>(lpn, p, grid_cap, st);
+        case 1: return launch_mttkrp_lpn<T, VEC, 1, RES>(lpn, p, grid_cap, st);
+        case 2: return launch_mttkrp_lpn<T, VEC, 2, RES>(lpn, p, grid_cap, st);
+        case 3: return launch_mttkrp_lpn<T, VEC, 3, RES>(lpn, p, grid_cap, st);
+        case 4: return launch_mttkrp_lpn<T, VEC, 4, RES>(lpn, p, grid_cap, st);
         default: return (int)cudaErrorInvalidValue;
     }
 }
 
-template <typename T>
+template <typename T, bool RES>
 static int launch_mttkrp_t(int nin, const MttkrpParams& p, int grid_cap, cudaStream_t st) {
     const int vec = Shape<T>::vec(p.R);
     const int lpn = Shape<T>::lpn(p.R, vec);
-    if (vec == Shape<T>::kVec) return launch_mttkrp_nin<T, Shape<T>::kVec>(nin, lpn, p, grid_cap, st);
-    if (vec == 1) return launch_mttkrp_nin<T, 1>(nin, lpn, p, grid_cap, st);
+    if (vec == Shape<T>::kVec) return launch_mttkrp_nin<T, Shape<T>::kVec, RES>(nin, lpn, p, grid_cap, st);
+    if (vec == 1) return launch_mttkrp_nin<T, 1, RES>(nin, lpn, p, grid_cap, st);
     return (int)cudaErrorInvalidValue;
 }
 
@@ -125,6 +126,7 @@ static int launch_sample_nm(int lpn, const SampleParams& p, cudaStream_t st) {
         case 2: return launch_sample_lpn<T, VEC, 2>(lpn, p, st);
         case 3: return launch_sample_lpn<T, VEC, 3>(lpn, p, st);
         case 4: return launch_sample_lpn<T, VEC, 4>(lpn, p, st);
+        case 5: return launch_sample_lpn<T, VEC, 5>(lpn, p, st);
         default: return (int)cudaErrorInvalidValue;
     }
 }
@@ -144,7 +146,10 @@ static int launch_sample_t(const SampleParams& p, cudaStream_t st) {
 #define AMPED_DEFINE_DTYPE_LAUNCHERS(T, SUFFIX)                                                               \
     namespace amped {                                                                                       \
     int launch_mttkrp_##SUFFIX(int nin, const MttkrpParams& p, int grid_cap, void* st) {                    \
-        return launch_mttkrp_t<T>(nin, p, grid_cap, static_cast<cudaStream_t>(st));                        \
+        return launch_mttkrp_t<T, false>(nin, p, grid_cap, static_cast<cudaStream_t>(st));                 \
+    }                                                                                                       \
+    int launch_residual_##SUFFIX(int nin, const MttkrpParams& p, int grid_cap, void* st) {                  \
+        return launch_mttkrp_t<T, true>(nin, p, grid_cap, static_cast<cudaStream_t>(st));                  \
     }                                                                                                       \
     int launch_sample_##SUFFIX(const SampleParams& p, void* st) {                                           \
         return launch_sample_t<T>(p, static_cast<cudaStream_t>(st));                                        \

@@ -285,6 +285,73 @@ __device__ __forceinline__ void store_part(float* dst, const float (&a)[VEC], bo
     }
 }
 
+// ------------------------------------------------------------------ residual (completion) helpers
+// t[e] = prod_n x_n[e] in fp32 (the Khatri-Rao row of one nonzero, without its value).
+template <typename T, int VEC, int NIN>
+__device__ __forceinline__ void kr_row(float (&t)[VEC], const Raw<T, VEC> (&x)[NIN]) {
+    if constexpr (std::is_same<T, float>::value && VEC == 8) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            unsigned long long pr = pk(__uint_as_float(x[0].w[2 * k]), __uint_as_float(x[0].w[2 * k + 1]));
+#pragma unroll
+            for (int n = 1; n < NIN; ++n)
+                pr = mul2(pr, pk(__uint_as_float(x[n].w[2 * k]), __uint_as_float(x[n].w[2 * k + 1])));
+            upk(pr, t[2 * k], t[2 * k + 1]);
+        }
+    } else if constexpr (VEC == 16) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float lo, hi;
+            if constexpr (NIN == 1) {
+                lo = lo_f(x[0].w[i], (const T*)nullptr);
+                hi = hi_f(x[0].w[i], (const T*)nullptr);
+            } else {
+                if constexpr (std::is_same<T, __nv_bfloat16>::value)
+                    prod_bf16(x[0].w[i], x[1].w[i], lo, hi);
+                else
+                    prod_f16(x[0].w[i], x[1].w[i], lo, hi);
+#pragma unroll
+                for (int n = 2; n < NIN; ++n) {
+                    lo *= lo_f(x[n].w[i], (const T*)nullptr);
+                    hi *= hi_f(x[n].w[i], (const T*)nullptr);
+                }
+            }
+            t[2 * i] = lo;
+            t[2 * i + 1] = hi;
+        }
+    } else {
+        float pr = x[0].f;
+#pragma unroll
+        for (int n = 1; n < NIN; ++n) pr *= x[n].f;
+        t[0] = pr;
+    }
+}
+
+// Sum over the group's LPN lanes of sum_e a[e] * b[e]: the sampled model value
+// of one nonzero (a = its Khatri-Rao row, b = the output-mode factor row).
+template <int VEC, int LPN>
+__device__ __forceinline__ float group_dot(const float (&a)[VEC], const float (&b)[VEC]) {
+    float d = 0.f;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) d = fmaf(a[e], b[e], d);
+#pragma unroll
+    for (int o = 1; o < LPN; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    return d;
+}
+
+// The lane's slice of output-mode factor row `row` (zeros for lanes beyond R).
+template <typename T, int VEC>
+__device__ __forceinline__ void load_out_row(const MttkrpParams& p, int row, int q, float (&a)[VEC]) {
+    if (q * VEC < p.R) {
+        Raw<T, VEC> r;
+        r.load(static_cast<const T*>(p.fout) + (int64_t)row * p.R + q * VEC);
+        widen(r, a);
+    } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) a[e] = 0.f;
+    }
+}
+
 // ------------------------------------------------------------------ MTTKRP
 // Steps per chunk: all gathers of a chunk are issued before any use.  Four
 // steps at 64 registers (4 blocks of 256 threads per SM) measured fastest on
@@ -330,32 +397,58 @@ __device__ __forceinline__ void prefetch_batch(const MttkrpParams& p, int kb, in
     }
 }
 
-// Shared-memory staging of one stream batch per warp, one 16-byte record per
-// nonzero: the NIN input coordinates and the value (bit pattern) in the last word.
-// Record j lives in slot j ^ ((j >> 3) & 7): with that swizzle the staging
-// stores (lane l writes records 4l..4l+3) and the per-step loads (G consecutive
-// records) both touch every 16-byte bank group at most once per 128 bytes.
-struct WarpStage {
-    int4 rec[kBatch];
-};
+// Shared-memory staging of one stream batch per warp, one record per nonzero:
+// the NIN input coordinates and the value's bit pattern, 16 bytes for up to
+// three input modes ({i0, i1, i2, v}), 32 bytes for four ({i0..i3}, {v, -, -, -}).
+// Record j lives in slot j ^ ((j >> 3) & 7) of each 16-byte array: with that
+// swizzle the staging stores (lane l writes records 4l..4l+3) and the per-step
+// loads (G consecutive records) both touch every 16-byte bank group at most
+// once per 128 bytes.
 __device__ __forceinline__ int swz(int j) { return j ^ ((j >> 3) & 7); }
 
 template <int NIN>
-__device__ __forceinline__ void stage_batch(WarpStage& st, int lane, const StreamBatch<NIN>& b) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        int4 r;
-        r.x = comp_rt(b.idx[0], c);
-        r.y = NIN > 1 ? comp_rt(b.idx[NIN > 1 ? 1 : 0], c) : 0;
-        r.z = NIN > 2 ? comp_rt(b.idx[NIN > 2 ? 2 : 0], c) : 0;
-        r.w = __float_as_int(comp_rt(b.val, c));
-        st.rec[swz(4 * lane + c)] = r;
-    }
-}
+struct Rec {
+    int4 a;
+    __device__ __forceinline__ int idx(int n) const { return n == 0 ? a.x : n == 1 ? a.y : a.z; }
+    __device__ __forceinline__ float val() const { return __int_as_float(a.w); }
+};
+template <>
+struct Rec<4> {
+    int4 a, b;
+    __device__ __forceinline__ int idx(int n) const { return comp_rt(a, n); }
+    __device__ __forceinline__ float val() const { return __int_as_float(b.x); }
+};
 
 template <int NIN>
-__device__ __forceinline__ int rec_idx(const int4& r, int n) {
-    return n == 0 ? r.x : n == 1 ? r.y : r.z;
+struct WarpStage {
+    int4 a[kBatch];
+    __device__ __forceinline__ Rec<NIN> get(int j) const { return Rec<NIN>{a[swz(j)]}; }
+};
+template <>
+struct WarpStage<4> {
+    int4 a[kBatch];
+    int4 b[kBatch];
+    __device__ __forceinline__ Rec<4> get(int j) const { return Rec<4>{a[swz(j)], b[swz(j)]}; }
+};
+
+template <int NIN>
+__device__ __forceinline__ void stage_batch(WarpStage<NIN>& st, int lane, const StreamBatch<NIN>& b) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int slot = swz(4 * lane + c);
+        if constexpr (NIN <= 3) {
+            int4 r;
+            r.x = comp_rt(b.idx[0], c);
+            r.y = NIN > 1 ? comp_rt(b.idx[NIN > 1 ? 1 : 0], c) : 0;
+            r.z = NIN > 2 ? comp_rt(b.idx[NIN > 2 ? 2 : 0], c) : 0;
+            r.w = __float_as_int(comp_rt(b.val, c));
+            st.a[slot] = r;
+        } else {
+            st.a[slot] = make_int4(comp_rt(b.idx[0], c), comp_rt(b.idx[1], c), comp_rt(b.idx[2], c),
+                                   comp_rt(b.idx[3], c));
+            st.b[slot] = make_int4(__float_as_int(comp_rt(b.val, c)), 0, 0, 0);
+        }
+    }
 }
 
 // One warp processes one segment.  The warp holds G = 32/LPN groups; at
@@ -365,9 +458,9 @@ __device__ __forceinline__ int rec_idx(const int4& r, int n) {
 // gathers and multiply-adds straight into the row accumulator); other chunks
 // stage their products and close rows that end inside a step with a
 // butterfly sum over the groups.
-template <typename T, int VEC, int LPN, int NIN>
-__device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, WarpStage& st, int lane,
-                                               const T* const (&fl)[NIN]) {
+template <typename T, int VEC, int LPN, int NIN, bool RES>
+__device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, WarpStage<NIN>& st, int lane,
+                                               const T* const (&fl)[NIN], double& lsum) {
     constexpr int G = 32 / LPN;
     constexpr int CH = Chunk<VEC>::value;
     constexpr int CHN = CH * G;  // nonzeros per chunk
@@ -399,6 +492,10 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
     float acc[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+    float ao[RES ? VEC : 1];  // residual mode: output-mode factor row of row i
+    if constexpr (RES) {
+        if (i < p.I) load_out_row<T, VEC>(p, __ldg(p.rows_L + i), q, ao);
+    }
 
     auto flush = [&](int row) {
         const int64_t rq = (int64_t)(lane % LPN) * VEC;
@@ -443,6 +540,9 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
         } else {
             rend = nz_e;
         }
+        if constexpr (RES) {
+            if (i < p.I && rend > rstart) load_out_row<T, VEC>(p, __ldg(p.rows_L + i), q, ao);
+        }
     };
 
     int kb = nz_s & ~3;
@@ -462,14 +562,38 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
             if (base + CHN <= nz_s) continue;
             if (base >= nz_s && base + CHN <= nz_e && base + CHN <= rend) {
                 // fast path: every nonzero of the chunk is valid and in row i
-                if (active) {
+                if constexpr (!RES) {
+                    if (active) {
+#pragma unroll
+                        for (int u = 0; u < CH; ++u) {
+                            const Rec<NIN> r = st.get(c0 + u * G + g);
+                            Raw<T, VEC> x[NIN];
+#pragma unroll
+                            for (int n = 0; n < NIN; ++n)
+                                x[n].load(fl[n] + (uint64_t)(uint32_t)r.idx(n) * R);
+                            Mac<T, VEC, NIN>::run(acc, r.val(), x);
+                        }
+                    }
+                } else {
+                    // residual mode: value r = (model at the nonzero) - x, contribution r * KR row
 #pragma unroll
                     for (int u = 0; u < CH; ++u) {
-                        const int4 r = st.rec[swz(c0 + u * G + g)];
-                        Raw<T, VEC> x[NIN];
+                        const Rec<NIN> r = st.get(c0 + u * G + g);
+                        float t[VEC];
+                        if (active) {
+                            Raw<T, VEC> x[NIN];
 #pragma unroll
-                        for (int n = 0; n < NIN; ++n) x[n].load(fl[n] + (uint64_t)(uint32_t)rec_idx<NIN>(r, n) * R);
-                        Mac<T, VEC, NIN>::run(acc, __int_as_float(r.w), x);
+                            for (int n = 0; n < NIN; ++n)
+                                x[n].load(fl[n] + (uint64_t)(uint32_t)r.idx(n) * R);
+                            kr_row<T, VEC, NIN>(t, x);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) t[e] = 0.f;
+                        }
+                        const float res = group_dot<VEC, LPN>(t, ao) - r.val();
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) acc[e] = fmaf(res, t[e], acc[e]);
+                        if (q == 0) lsum += (double)res * (double)res;
                     }
                 }
                 continue;
@@ -479,20 +603,25 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
 #pragma unroll
             for (int h = 0; h < CH; h += SH) {
                 float t[SH][VEC];
+                float vv[RES ? SH : 1];  // residual mode: the staged products omit the value
 #pragma unroll
                 for (int u = 0; u < SH; ++u) {
                     const int j = c0 + (h + u) * G + g;
                     const int k = kb + j;
                     const bool valid = active && k >= nz_s && k < nz_e;
-                    const int4 r = st.rec[swz(j)];
+                    const Rec<NIN> r = st.get(j);
 #pragma unroll
                     for (int e = 0; e < VEC; ++e) t[u][e] = 0.f;
+                    if constexpr (RES) vv[u] = r.val();
                     if (valid) {
                         Raw<T, VEC> x[NIN];
 #pragma unroll
                         for (int n = 0; n < NIN; ++n)
-                            x[n].load(fl[n] + (uint64_t)(uint32_t)rec_idx<NIN>(r, n) * R);
-                        Mac<T, VEC, NIN>::run(t[u], __int_as_float(r.w), x);
+                            x[n].load(fl[n] + (uint64_t)(uint32_t)r.idx(n) * R);
+                        if constexpr (RES)
+                            kr_row<T, VEC, NIN>(t[u], x);
+                        else
+                            Mac<T, VEC, NIN>::run(t[u], r.val(), x);
                     }
                 }
 #pragma unroll
@@ -501,16 +630,26 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
                     if (kstep >= nz_e) break;
                     const int klast = min(kstep + G, nz_e) - 1;
                     if (klast < nz_s) continue;
-                    if (kstep >= rstart && klast < rend) {  // the whole step lies in row i
+                    if constexpr (!RES) {
+                        if (kstep >= rstart && klast < rend) {  // the whole step lies in row i
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e) acc[e] += t[u][e];
-                        continue;
+                            for (int e = 0; e < VEC; ++e) acc[e] += t[u][e];
+                            continue;
+                        }
                     }
                     const int kg = kstep + g;
                     while (true) {
-                        const bool in = kg >= rstart && kg < rend;
+                        const bool in = kg >= rstart && kg < rend && kg >= nz_s && kg < nz_e;
+                        if constexpr (RES) {
+                            // the model value needs the output-mode row of the nonzero's own row
+                            const float res = group_dot<VEC, LPN>(t[u], ao) - vv[u];
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e) acc[e] += in ? t[u][e] : 0.f;
+                            for (int e = 0; e < VEC; ++e) acc[e] = in ? fmaf(res, t[u][e], acc[e]) : acc[e];
+                            if (in && q == 0) lsum += (double)res * (double)res;
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) acc[e] += in ? t[u][e] : 0.f;
+                        }
                         if (klast < rend) break;
                         advance();
                     }
@@ -526,9 +665,9 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
 // One short segment: at most kShortRows rows (sorted by length, so rows of a
 // round have similar lengths) whose nonzeros fit one staged batch.  Group g
 // accumulates row r0+g by itself and stores it: no cross-group reduction.
-template <typename T, int VEC, int LPN, int NIN>
-__device__ __forceinline__ void mttkrp_short(const MttkrpParams& p, int t, WarpStage& st, int lane,
-                                             const T* const (&fl)[NIN]) {
+template <typename T, int VEC, int LPN, int NIN, bool RES>
+__device__ __forceinline__ void mttkrp_short(const MttkrpParams& p, int t, WarpStage<NIN>& st, int lane,
+                                             const T* const (&fl)[NIN], double& lsum) {
     constexpr int G = 32 / LPN;
     const int g = lane / LPN, q = lane % LPN;
     const bool active = q * VEC < p.R;
@@ -554,34 +693,66 @@ __device__ __forceinline__ void mttkrp_short(const MttkrpParams& p, int t, WarpS
         float acc[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-        for (int k = 0; k < maxlen; k += 2) {
+        const int id = __shfl_sync(0xffffffffu, my_id, rr & 31);
+        if constexpr (!RES) {
+            for (int k = 0; k < maxlen; k += 2) {
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                if (active && k + u < len) {
-                    const int4 r = st.rec[swz(start + k + u - kb)];
+                for (int u = 0; u < 2; ++u) {
+                    if (active && k + u < len) {
+                        const Rec<NIN> r = st.get(start + k + u - kb);
+                        Raw<T, VEC> x[NIN];
+#pragma unroll
+                        for (int n = 0; n < NIN; ++n)
+                            x[n].load(fl[n] + (uint64_t)(uint32_t)r.idx(n) * R);
+                        Mac<T, VEC, NIN>::run(acc, r.val(), x);
+                    }
+                }
+            }
+        } else {
+            float ao[VEC];
+            if (rr < nr) {
+                load_out_row<T, VEC>(p, id, q, ao);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) ao[e] = 0.f;
+            }
+            for (int k = 0; k < maxlen; ++k) {
+                const bool in = k < len;
+                const Rec<NIN> r = st.get(in ? start + k - kb : 0);
+                float tt[VEC];
+                if (active && in) {
                     Raw<T, VEC> x[NIN];
 #pragma unroll
-                    for (int n = 0; n < NIN; ++n) x[n].load(fl[n] + (uint64_t)(uint32_t)rec_idx<NIN>(r, n) * R);
-                    Mac<T, VEC, NIN>::run(acc, __int_as_float(r.w), x);
+                    for (int n = 0; n < NIN; ++n) x[n].load(fl[n] + (uint64_t)(uint32_t)r.idx(n) * R);
+                    kr_row<T, VEC, NIN>(tt, x);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) tt[e] = 0.f;
+                }
+                const float res = group_dot<VEC, LPN>(tt, ao) - r.val();
+                if (in) {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) acc[e] = fmaf(res, tt[e], acc[e]);
+                    if (q == 0) lsum += (double)res * (double)res;
                 }
             }
         }
-        const int id = __shfl_sync(0xffffffffu, my_id, rr & 31);
         if (rr < nr && active) store_row<VEC>(p.out + (int64_t)id * R + q * VEC, acc, true);
     }
     __syncwarp();  // the stage is reused by the warp's next segment
 }
 
-template <typename T, int VEC, int LPN, int NIN>
-__global__ void __launch_bounds__(256, 4) mttkrp_kernel(const MttkrpParams p) {
-    __shared__ __align__(16) WarpStage stage[8];
+template <typename T, int VEC, int LPN, int NIN, bool RES>
+__global__ void __launch_bounds__(256, RES ? 2 : 4) mttkrp_kernel(const MttkrpParams p) {
+    __shared__ __align__(16) WarpStage<NIN> stage[8];
     const int lane = threadIdx.x & 31;
-    WarpStage& st = stage[threadIdx.x >> 5];
+    WarpStage<NIN>& st = stage[threadIdx.x >> 5];
     const int q = lane % LPN;
     const T* fl[NIN];  // this lane's first rank in every input factor
 #pragma unroll
     for (int n = 0; n < NIN; ++n) fl[n] = static_cast<const T*>(p.fac[n]) + q * VEC;
     const int total = p.S + p.S_S;  // long segments first, then short segments
+    double lsum = 0.0;  // residual mode: this lane's share of sum (m - x)^2
     int s = 0;
     if (lane == 0) s = atomicAdd(p.queue, 1);
     s = __shfl_sync(0xffffffffu, s, 0);
@@ -589,10 +760,17 @@ __global__ void __launch_bounds__(256, 4) mttkrp_kernel(const MttkrpParams p) {
         int nxt = 0;
         if (lane == 0) nxt = atomicAdd(p.queue, 1);  // next ticket, latency hidden by this segment
         if (s < p.S)
-            mttkrp_segment<T, VEC, LPN, NIN>(p, s, st, lane, fl);
+            mttkrp_segment<T, VEC, LPN, NIN, RES>(p, s, st, lane, fl, lsum);
         else
-            mttkrp_short<T, VEC, LPN, NIN>(p, s - p.S, st, lane, fl);
+            mttkrp_short<T, VEC, LPN, NIN, RES>(p, s - p.S, st, lane, fl, lsum);
         s = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+    if constexpr (RES) {
+        if (p.loss != nullptr) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            if (lane == 0 && lsum != 0.0) atomicAdd(p.loss, 0.5 * lsum);
+        }
     }
 }
 

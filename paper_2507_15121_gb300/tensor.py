@@ -174,6 +174,18 @@ class Tensor:
                                             _stream_ptr(stream)))
         return grads
 
+    def completion_grad(self, factors, grads=None, loss=None, stream=None):
+        """Fused gradient of L = 1/2 sum_k (m_k - x_k)^2 over the tensor's own values x:
+        returns (grads, loss) with loss a 0-dim float64 CUDA tensor."""
+        fp, code, R = self._factors(factors)
+        grads = [self._out(n, R, None if grads is None else grads[n]) for n in range(self.nmodes)]
+        if loss is None:
+            loss = torch.empty((), dtype=torch.float64, device=self.device)
+        gp = _lib.ptr_array([g.data_ptr() for g in grads])
+        _lib.check(_lib.lib().amped_cp_completion_grad(self.handle, fp, code, R, gp, loss.data_ptr(),
+                                                       _stream_ptr(stream)))
+        return grads, loss
+
     def set_kernel_events(self, start, stop) -> None:
         """Record torch.cuda.Event `start`/`stop` around the next MTTKRP kernel."""
         for ev in (start, stop):

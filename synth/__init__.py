@@ -115,6 +115,9 @@ WORKLOADS = {
     "zipf3_r64": Workload("zipf3_r64", (10_000_000, 5_000_000, 2_000_000), 200_000_000,
                           (("zipf", 1.1),) * 3, rank=64, seed=20250715 + 2,
                           note="same tensor as zipf3 at R=64 for 16-bit factor storage"),
+    "zipf5": Workload("zipf5", (15_500_000, 6_200_000, 784_000, 6_100, 6_100), 500_000_000,
+                      (("zipf", 1.1),) * 5, rank=32, seed=20250715 + 6,
+                      note="5-mode power-law with the shape of the paper's Twitch tensor (Table 3)"),
     "planted3": Workload("planted3", (5_000_000, 2_000_000, 1_000_000), 100_000_000, (("zipf", 1.1),) * 3,
                          rank=32, seed=20250715 + 5, planted_rank=16, noise_sd=0.01, factor_scale=0.5,
                          note="completion: planted rank-16 CP values plus N(0, 0.01^2) noise"),

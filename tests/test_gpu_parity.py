@@ -73,6 +73,26 @@ def test_zipf4_reduced_fp32():
     check_fp32(c, F)
 
 
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16])
+def test_zipf5_five_modes(dt):
+    """5-mode power-law tensor with the Twitch tensor's shape (scaled), all modes."""
+    w = synth.WORKLOADS["zipf5"].scaled(0.0004)
+    c = synth.make(w)
+    F = synth.factors(c.dims, 32, w.seed)
+    got, Fd = run_all(c, F, dtype=dt)
+    if dt == torch.float32:
+        refs = [oracle.mttkrp(c.dims, c.idx, c.vals, F, m) for m in range(5)]
+    else:
+        bits = [host_bits(f) for f in Fd]
+        refs = [oracle.mttkrp(c.dims, c.idx, c.vals, bits, m, "bf16") for m in range(5)]
+    for m in range(5):
+        assert oracle.row_error(got[m], refs[m]) <= FP32_BAR, m
+    t = amped.Tensor(c.dims, c.idx, c.vals)
+    m_gpu = t.cp_sample([dev(f) for f in F]).cpu().numpy()
+    m_ref = oracle.cp_sample(c.dims, c.idx, F)
+    assert np.max(np.abs(m_gpu - m_ref) / np.abs(m_ref)) <= FP32_BAR
+
+
 @pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
 @pytest.mark.parametrize("R", [32, 64])
 def test_zipf3_16bit_factors(dt, R):
@@ -256,7 +276,67 @@ def test_planted_model_residual_is_noise():
     assert abs(resid.std() - w.noise_sd) < 0.1 * w.noise_sd
 
 
+def _planted(scale, dims_override=None):
+    w = synth.WORKLOADS["planted3"].scaled(scale)
+    c = synth.make(w)
+    x = (oracle.cp_sample(c.dims, c.idx, c.extra["planted_factors"]) + c.extra["noise"]).astype(np.float32)
+    F = synth.factors(c.dims, 32, w.seed, scale=w.factor_scale)
+    return w, c, x, F
+
+
+@pytest.mark.parametrize("short_rows", [0, -1])
+def test_fused_completion_grad_against_oracle(short_rows):
+    """amped_cp_completion_grad: one fused pass per mode (model value rebuilt from the
+    output-mode row) against the FP64 oracle's completion gradient and loss."""
+    w, c, x, F = _planted(0.0005)
+    t = amped.Tensor(c.dims, c.idx, x, short_rows=short_rows)
+    Fd = [dev(f) for f in F]
+    grads, loss = t.completion_grad(Fd)
+    L_ref, G_ref = oracle.completion_grad(c.dims, c.idx, x, F)
+    assert abs(loss.item() - L_ref) <= 1e-5 * L_ref
+    for n in range(3):
+        assert oracle.row_error(grads[n].cpu().numpy(), G_ref[n], floor_frac=1e-6) <= GRAD_BAR
+    # the generic gradient with residual values gives the same result
+    m = t.cp_sample(Fd)
+    generic = t.cp_grad(Fd, (m - dev(x)).contiguous())
+    for n in range(3):
+        assert oracle.row_error(grads[n].cpu().numpy(), generic[n].cpu().numpy().astype(np.float64),
+                                floor_frac=1e-6) <= GRAD_BAR
+
+
+def test_fused_completion_grad_bf16_and_autograd():
+    w, c, x, F = _planted(0.0003)
+    t = amped.Tensor(c.dims, c.idx, x)
+    Fb = [dev(f, torch.bfloat16) for f in F]
+    grads, loss = t.completion_grad(Fb)
+    bits = [host_bits(f) for f in Fb]
+    m = oracle.cp_sample(c.dims, c.idx, bits, "bf16")
+    G_ref = oracle.cp_grad(c.dims, c.idx, m - x.astype(np.float64), bits, "bf16")
+    for n in range(3):
+        assert oracle.row_error(grads[n].cpu().numpy(), G_ref[n], floor_frac=1e-6) <= GRAD_BAR
+    # autograd through the fused loss equals the two-kernel autograd path
+    Fa = [dev(f).requires_grad_(True) for f in F]
+    Fg = [dev(f).requires_grad_(True) for f in F]
+    la = amped.fused_completion_loss(t, Fa)
+    la.backward()
+    lg = amped.completion_loss(t, Fg, dev(x))
+    lg.backward()
+    assert abs(la.item() - lg.item()) <= 1e-5 * lg.item()
+    for n in range(3):
+        assert oracle.row_error(Fa[n].grad.cpu().numpy(), Fg[n].grad.cpu().numpy().astype(np.float64),
+                                floor_frac=1e-6) <= GRAD_BAR
+
+
 # --------------------------------------------------------------------------- full size, sampled rows
+def oracle_rows_all_modes(c, F, rows):
+    """The oracle's sampled-row pass for every mode; the single-threaded passes of
+    different modes run side by side (ctypes releases the GIL during each call)."""
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=len(rows)) as ex:
+        futs = [ex.submit(oracle.mttkrp_rows, c.dims, c.idx, c.vals, F, m, rows[m]) for m in range(len(rows))]
+        return [f.result() for f in futs]
+
+
 def sampled_rows(c, mode, k, seed):
     counts = np.bincount(c.idx[:, mode], minlength=c.dims[mode])
     hot = np.argsort(-counts, kind="stable")[:16]
@@ -279,11 +359,12 @@ def test_zipf3_full_size_sampled_rows():
     outs_b = [o.cpu().numpy() for o in t.mttkrp_all(Fb)]
     del Fd, Fb
     t.close()
+    rows = [sampled_rows(c, m, 4096, w.seed) for m in range(3)]
+    refs = oracle_rows_all_modes(c, F, rows)
     for m in range(3):
-        rows = sampled_rows(c, m, 4096, w.seed)
-        ref = oracle.mttkrp_rows(c.dims, c.idx, c.vals, F, m, rows)
-        assert oracle.row_error(outs[m][rows], ref) <= FP32_BAR, m
-        assert oracle.row_error(outs_b[m][rows], ref) <= LOWP_BAR, m
+        ref = refs[m]
+        assert oracle.row_error(outs[m][rows[m]], ref) <= FP32_BAR, m
+        assert oracle.row_error(outs_b[m][rows[m]], ref) <= LOWP_BAR, m
         # rows that no nonzero touches are exactly zero
         counts = np.bincount(c.idx[:, m], minlength=c.dims[m])
         empty = np.flatnonzero(counts == 0)[:1000]
@@ -304,7 +385,7 @@ def test_zipf4_billion_full_size_sampled_rows():
     del Fd
     t.close()
     torch.cuda.empty_cache()
+    rows = [sampled_rows(c, m, 2048, w.seed) for m in range(4)]
+    refs = oracle_rows_all_modes(c, F, rows)
     for m in range(4):
-        rows = sampled_rows(c, m, 2048, w.seed)
-        ref = oracle.mttkrp_rows(c.dims, c.idx, c.vals, F, m, rows)
-        assert oracle.row_error(outs[m][rows], ref) <= FP32_BAR, m
+        assert oracle.row_error(outs[m][rows[m]], refs[m]) <= FP32_BAR, m
