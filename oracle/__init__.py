@@ -38,7 +38,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
+DTYPES = {"f32": 0, "bf16": 1, "f16": 2, "f64": 3}
 
 
 def build(force: bool = False) -> str:
@@ -70,9 +70,9 @@ def _ptr(a):
 
 
 def _storage(f: np.ndarray, dtype: str) -> np.ndarray:
-    """Factor in its storage form: float32, or raw uint16 bits for bf16/f16."""
-    if dtype == "f32":
-        assert f.dtype == np.float32
+    """Factor in its storage form: float32 / float64, or raw uint16 bits for bf16/f16."""
+    if dtype in ("f32", "f64"):
+        assert f.dtype == (np.float32 if dtype == "f32" else np.float64)
         return np.ascontiguousarray(f)
     assert f.dtype == np.uint16, "16-bit factors are passed as their raw uint16 bit patterns"
     return np.ascontiguousarray(f)

@@ -8,8 +8,8 @@
  *
  * Every routine is a plain, single-threaded loop over the nonzeros in the
  * order the caller gives them, accumulating in double precision.  Factor
- * entries are read in their storage type (fp32, bf16 or fp16) and widened
- * exactly to double.
+ * entries are read in their storage type (fp32, bf16, fp16, or fp64 for the
+ * ALS oracle) and widened exactly to double.
  *
  * What is computed (paper, Sec. 3 "Elementwise computation" and Alg. 2):
  *   for output mode d and each nonzero x at (i_0, ..., i_{N-1}),
@@ -23,11 +23,12 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_F32 = 0, ORC_BF16 = 1, ORC_F16 = 2 };
+enum { ORC_F32 = 0, ORC_BF16 = 1, ORC_F16 = 2, ORC_F64 = 3 };
 
 /* exact widening of one stored factor entry to double */
 static double widen(const void* base, int dtype, int64_t i) {
     if (dtype == ORC_F32) return (double)((const float*)base)[i];
+    if (dtype == ORC_F64) return ((const double*)base)[i];
     uint16_t h = ((const uint16_t*)base)[i];
     if (dtype == ORC_BF16) {
         /* bfloat16 is the upper half of an IEEE binary32 */
