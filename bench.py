@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the 16-bit factor variants")
+    ap.add_argument("--als-sweeps", type=int, default=5, help="timed CP-ALS sweeps (0 = skip)")
     ap.add_argument("--lowp", default="", help="16-bit factor variants to time, e.g. bf16,f16 "
                                               "(default: bf16; bf16,f16 for zipf3_r64)")
     return ap.parse_args()
@@ -270,6 +271,31 @@ def time_steps(t, Fd, K, W, torch, stream):
     return total, per_mode, launches
 
 
+def time_als(t, Fd, S, torch, stream):
+    """One initial CP-ALS sweep (Grams computed), then S timed sweeps from the
+    factors it left; returns (total ms, fit after each timed sweep, launches)."""
+    import paper_2507_15121_gb300 as amped
+    A = [f.clone() for f in Fd]
+    R = A[0].shape[1]
+    lam = torch.empty(R, device=A[0].device)
+    grams = torch.empty((t.nmodes, R, R), dtype=torch.float64, device=A[0].device)
+    stats = torch.zeros(8, dtype=torch.float64, device=A[0].device)
+    t.cp_als_sweep(A, lam, grams, stats, init=True, stream=stream)
+    hist = torch.empty((S, 8), dtype=torch.float64, device=A[0].device)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    l0 = amped.kernel_launches()
+    start.record(stream)
+    for s in range(S):
+        t.cp_als_sweep(A, lam, grams, stats, stream=stream)
+        hist[s].copy_(stats)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    launches = amped.kernel_launches() - l0
+    return start.elapsed_time(stop), [float(v) for v in hist[:, 0].cpu()], launches
+
+
 def run_ours(args, w, world, rank, local, pg):
     import torch
     import paper_2507_15121_gb300 as amped
@@ -300,6 +326,7 @@ def run_ours(args, w, world, rank, local, pg):
             Fl = [f.to(tdt[name]) for f in Fd]
             lowp_res[name] = time_steps(t, Fl, K, W, torch, stream)
             del Fl
+        als_res = time_als(t, Fd, args.als_sweeps, torch, stream) if args.als_sweeps > 0 and w.rank <= 64 else None
     barrier(pg, device)
     total = max_over_ranks(total, pg, device)
 
@@ -332,6 +359,16 @@ def run_ours(args, w, world, rank, local, pg):
                          "traffic": None, "kernel": kernel_name("__nv_bfloat16" if name == "bf16" else "__half",
                                                                 w.rank, c.nmodes),
                          "algorithmic_bytes_per_mode": Bl, "kernel_ms_per_mode": kl}}
+
+    if als_res is not None:
+        ms, fits, launches_a = als_res
+        ms = max_over_ranks(ms, pg, device)
+        line["variants"] = line.get("variants", {})
+        line["variants"]["cp_als_sweep"] = {
+            "value": world * c.nnz * args.als_sweeps / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_sweep": ms / args.als_sweeps, "sweeps": args.als_sweeps, "gpu_launches": launches_a,
+            "fit_per_sweep": fits, "path": "amped_cp_als_sweep (MTTKRP, Gram, fp64 Cholesky solve, apply per mode)",
+            "dense_steps_ms_per_sweep": ms / args.als_sweeps - total / K}
 
     # end to end through the host-buffer entry point: factors in, outputs out, every step
     if not args.no_e2e:

@@ -162,6 +162,42 @@ amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_d
 amped_status amped_cp_completion_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
                                       float* const* grads, double* loss, void* stream);
 
+/*
+ * ||X||^2 of the tensor given to amped_tensor_create, with repeated coordinates summed into one
+ * entry (fp64, computed on the host at create time).  *norm2 is a host double.
+ */
+amped_status amped_tensor_norm2(amped_tensor_t t, double* norm2);
+
+/* amped_cp_als_sweep flag: compute grams[n] = A_n^T A_n of the given factors before the sweep. */
+#define AMPED_ALS_INIT 1
+
+/*
+ * One sweep of CP decomposition by alternating least squares (paper Sec. 2.1: ALS performs the
+ * mode-wise MTTKRPs of Eq. 1 in turn; the least-squares update after each MTTKRP is the standard
+ * CP-ALS normal-equation step, which the paper does not spell out).  For d = 0 .. N-1, each step
+ * seeing the factors updated before it:
+ *   M      = MTTKRP_d(X; A_n, n != d)                           (amped_mttkrp, fp32)
+ *   V      = Hadamard product over n != d of grams[n]           (fp64)
+ *   B      = M V^-1                                             (fp64 Cholesky of V; fp32 apply)
+ *   lambda = column 2-norms of B;  A_d = B with unit-norm columns (a zero column stays zero)
+ *   grams[d] = A_d^T A_d                                        (fp64)
+ * then the fit of the model X^ = [[lambda; A_0, ..., A_{N-1}]]:
+ *   stats[0] = 1 - ||X - X^|| / ||X||        stats[1] = ||X - X^||^2 (clamped at 0)
+ *   stats[2] = ||X||^2                       stats[3] = <X, X^>      stats[4] = ||X^||^2
+ *   stats[5] = modes whose V was singular in this sweep (their factor, Gram and lambda are left
+ *              unchanged; a singular last mode sets stats[0..4] to NaN)
+ *   stats[6] = first such mode + 1, or 0
+ * factors: host array of N device pointers [dims[n]][R] fp32, 16-byte aligned (32-byte when R is
+ *          a multiple of 8), updated in place.
+ * lambda:  device [R] fp32, written.   grams: device [N][R][R] fp64; on entry the Grams of the
+ * factors (or pass AMPED_ALS_INIT to compute them), on return those of the updated factors.
+ * stats:   device [8] fp64.  1 <= R <= 64 (R > 32 a multiple of 8); 2 to 5 modes.
+ * The MTTKRP output, its Gram and the solve's result live in workspace the handle allocates on
+ * first use (dims_max x R fp32).  Asynchronous: read stats after synchronising the stream.
+ */
+amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, float* lambda, double* grams,
+                                double* stats, int flags, void* stream);
+
 /* Sizes of a mode's plan (amped_plan_mode). */
 typedef struct {
     int64_t nnz, rows;                    /* nonzeros; rows of the mode (dims[mode]) */

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libamped.so")
 
 OK, ERR_INVALID, ERR_INDEX, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 F32, BF16, F16 = 0, 1, 2
+ALS_INIT = 1  # amped_cp_als_sweep flag: compute the Grams of the given factors first
 MAX_MODES = 8
 
 _STATUS = {OK: "ok", ERR_INVALID: "invalid argument", ERR_INDEX: "index out of range", ERR_OOM: "out of memory",
@@ -63,6 +64,8 @@ def lib() -> ctypes.CDLL:
             "amped_cp_completion_grad": ([vp, vp, c_int, c_int, vp, vp, vp], st),
             "amped_plan_mode": ([i64, c_int, vp, vp, c_int, c_int, c_int, c_int, ctypes.POINTER(PlanSizes)]
                                 + [vp] * 9, st),
+            "amped_tensor_norm2": ([vp, ctypes.POINTER(ctypes.c_double)], st),
+            "amped_cp_als_sweep": ([vp, vp, c_int, vp, vp, vp, c_int, vp], st),
             "amped_set_kernel_events": ([vp, vp, vp], st),
             "amped_kernel_launches": ([], i64),
             "amped_last_error": ([], ctypes.c_char_p),

@@ -1,0 +1,574 @@
+// als.cu — the dense steps of a CP-ALS sweep around the MTTKRP kernel.
+//
+// CP decomposition by alternating least squares (Sec. 2.1: ALS performs the
+// mode-wise MTTKRPs of Eq. 1 in turn, iteratively).  After the mode-d MTTKRP
+// M = X_(d) (Khatri-Rao of the other factors) the factor is the least-squares
+// solution A_d = M V^-1 with V the Hadamard product of the other factors'
+// Gram matrices; its columns are then scaled to unit norm and the norms kept
+// as lambda.  Per mode the library runs:
+//
+//   solve_kernel   one block, fp64:            V = Hadamard of the other Grams,
+//                                              Cholesky V = L L^T, W = V^-1
+//                                              (written as fp32)
+//   apply_kernel   norm pass: lambda_r = ||(M W)_r||, from the same fp32
+//                  products the apply pass uses (nothing stored);
+//                  apply pass: A_d = M W diag(1/lambda) stored, fp32, 4x4
+//                  register tiles (packed f32x2 FMA); the same pass
+//                  accumulates the Gram of the stored A_d and
+//                  ip_r = sum_i M(i,r) A_d(i,r)
+//   finish_kernel  one block: commits the new Gram; after the last mode, the fit
+//   gram_kernel    A^T A of the starting factors (first sweep only)
+//
+// Sums: fp32 over a tile, compensated (Kahan) fp32 across tiles, fp64 across
+// blocks.  lambda is never derived from a quadratic form in V^-1 (which
+// cancels catastrophically when V is ill-conditioned, as it is for the small
+// modes of power-law tensors).
+//
+// The fit is that of the model actually stored, [[lambda; A_0..A_{N-1}]]:
+//   <X, X^>  = sum_r lambda_r ip_r             (MTTKRP identity, last mode)
+//   ||X^||^2 = sum_{r,s} lambda_r lambda_s prod_n G_n(r,s)
+// with every G_n the Gram of the stored fp32 factor.  The closed forms that
+// hold at the exact least-squares optimum (<X, X^> = tr(Gm V^-1)) are not
+// used: they amplify the fp32 rounding of M by cond(V).
+// Ranks up to kAlsMaxRank; every loop over R is bounded by it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "amped_internal.h"
+
+namespace amped {
+namespace {
+
+constexpr int kAlsMaxRank = 64;
+
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float lo2(unsigned long long v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_float((uint32_t)(v >> 32)); }
+// (a.lo * b.lo + c.lo, a.hi * b.hi + c.hi), each rounded once
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Upper-triangle 4x4 tile k of an NT x NT tile grid, row-major: (ta, tb), ta <= tb.
+__device__ __forceinline__ void tri_tile(int k, int NT, int& ta, int& tb) {
+    ta = 0;
+    while (k >= NT - ta) {
+        k -= NT - ta;
+        ++ta;
+    }
+    tb = ta + k;
+}
+
+// Copies rows [base, base + nr) of the row-major [rows][R] matrix A into
+// tile[row * LD + col] (cols < R only; the padding columns are left alone).
+__device__ __forceinline__ void stage_rows(const float* __restrict__ A, int64_t base, int nr, int R, float* tile,
+                                           int LD) {
+    const float* src = A + base * R;
+    const int n = nr * R;
+    if ((R & 3) == 0) {
+        for (int e = threadIdx.x * 4; e < n; e += blockDim.x * 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(src + e));
+            const int row = e / R, col = e - row * R;
+            *reinterpret_cast<float4*>(tile + row * LD + col) = v;
+        }
+    } else {
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int row = e / R;
+            tile[row * LD + e - row * R] = __ldg(src + e);
+        }
+    }
+}
+
+// Per-thread share of an R x R Gram accumulated over staged row tiles: the 4x4
+// tiles on and above the diagonal, TILES threads per group, GROUPS groups per
+// block taking every GROUPS-th row.  Sums: fp32 over one tile's rows, Kahan
+// fp32 across tiles, fp64 across groups (fixed order) and blocks (atomics).
+template <int RP>
+struct GramAcc {
+    static constexpr int NT = RP / 4;
+    static constexpr int TILES = NT * (NT + 1) / 2;
+    static constexpr int GROUPS = 256 / TILES;
+    static_assert(GROUPS >= 1, "rank too large for one block");
+    int g, k, ta, tb;
+    float s[16], c[16];
+
+    __device__ __forceinline__ void init() {
+        g = threadIdx.x / TILES;
+        k = threadIdx.x - g * TILES;
+        tri_tile(k, NT, ta, tb);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) s[j] = c[j] = 0.f;
+    }
+    // rows [0, nr) of tile (row stride LD floats, padding columns zero)
+    __device__ __forceinline__ void add(const float* tile, int nr, int LD) {
+        if (g >= GROUPS) return;
+        unsigned long long acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = 0ull;
+        for (int i = g; i < nr; i += GROUPS) {
+            const float4 a = *reinterpret_cast<const float4*>(tile + i * LD + ta * 4);
+            const float4 b = *reinterpret_cast<const float4*>(tile + i * LD + tb * 4);
+            const unsigned long long b01 = pack2(b.x, b.y), b23 = pack2(b.z, b.w);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const unsigned long long aa = pack2(av[x], av[x]);
+                acc[2 * x] = ffma2(aa, b01, acc[2 * x]);
+                acc[2 * x + 1] = ffma2(aa, b23, acc[2 * x + 1]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {  // Kahan: s carries the sum, c its lost low part
+            const float part[2] = {lo2(acc[j]), hi2(acc[j])};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = 2 * j + h;
+                const float y = part[h] - c[q];
+                const float t = s[q] + y;
+                c[q] = (t - s[q]) - y;
+                s[q] = t;
+            }
+        }
+    }
+    // G[a][b] += this block's sums (every thread of the block calls this)
+    __device__ __forceinline__ void flush(double* red, double* __restrict__ G, int R) {
+        __syncthreads();
+        for (int gg = 0; gg < GROUPS; ++gg) {  // groups summed in a fixed order
+            if (g == gg)
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    red[k * 16 + j] = (gg ? red[k * 16 + j] : 0.0) + ((double)s[j] - (double)c[j]);
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < TILES * 16; e += blockDim.x) {
+            int ua, ub;
+            tri_tile(e / 16, NT, ua, ub);
+            const int a = ua * 4 + (e & 15) / 4, b = ub * 4 + (e & 3);
+            if (a < R && b < R) {
+                const double v = red[e];
+                atomicAdd(G + a * R + b, v);
+                if (ua != ub) atomicAdd(G + b * R + a, v);
+            }
+        }
+    }
+};
+
+// Rows per tile of gram_kernel (static shared memory stays under 48 KB).
+template <int RP>
+struct GramTile {
+    static constexpr int ROWS = RP == 64 ? 96 : 256;
+    static constexpr int LD = RP + 4;
+    static constexpr int V4 = ROWS * RP / 4 / 256;  // float4 per thread when R == RP
+};
+
+// G += A^T A for a row-major [rows][R] fp32 matrix.  RP = R rounded up to 8,
+// 16, 32 or 64.  When R is a multiple of 4 the next tile is loaded into
+// registers while the current one is summed.
+template <int RP>
+__global__ void __launch_bounds__(256, 2) gram_kernel(const float* __restrict__ A, int64_t rows, int R,
+                                                      double* __restrict__ G) {
+    using TL = GramTile<RP>;
+    constexpr int LD = TL::LD;
+    __shared__ __align__(16) float tile[TL::ROWS * LD];
+    __shared__ double red[GramAcc<RP>::TILES * 16];
+    GramAcc<RP> acc;
+    acc.init();
+    for (int e = threadIdx.x; e < TL::ROWS * LD; e += blockDim.x) tile[e] = 0.f;  // padding columns stay zero
+    const int64_t step = (int64_t)gridDim.x * TL::ROWS;
+    const bool vec = (R & 3) == 0;
+    float4 nxt[TL::V4];
+    auto fetch = [&](int64_t base) {
+        const int n = (int)((rows - base < TL::ROWS ? rows - base : TL::ROWS) * R);
+        const float* src = A + base * R;
+#pragma unroll
+        for (int j = 0; j < TL::V4; ++j) {
+            const int e = (threadIdx.x + j * 256) * 4;
+            if (e < n) nxt[j] = __ldg(reinterpret_cast<const float4*>(src + e));
+        }
+    };
+    int64_t base = (int64_t)blockIdx.x * TL::ROWS;
+    if (vec && base < rows) fetch(base);
+    for (; base < rows; base += step) {
+        const int nr = (int)(rows - base < TL::ROWS ? rows - base : TL::ROWS);
+        __syncthreads();
+        if (vec) {
+#pragma unroll
+            for (int j = 0; j < TL::V4; ++j) {
+                const int e = (threadIdx.x + j * 256) * 4;
+                if (e < nr * R) {
+                    const int row = e / R;
+                    *reinterpret_cast<float4*>(tile + row * LD + e - row * R) = nxt[j];
+                }
+            }
+            if (base + step < rows) fetch(base + step);
+        } else {
+            stage_rows(A, base, nr, R, tile, LD);
+        }
+        __syncthreads();
+        acc.add(tile, nr, LD);
+    }
+    acc.flush(red, G, R);
+}
+
+// One block of 256 threads; dynamic shared memory of 2 R (R+1) + 2 R doubles.
+// V = Hadamard of the other modes' Grams; Cholesky V = L L^T (right-looking);
+// Z = L^-1 (right-looking substitution); Y = V^-1 = Z^T Z, written as fp32 W.
+// Every step spreads its entries over the block; the only divisions are the
+// R reciprocals of the pivots.
+__global__ void __launch_bounds__(256) solve_kernel(AlsParams p) {
+    extern __shared__ double smem[];
+    const int R = p.R, LD = R + 1, tid = threadIdx.x, nth = blockDim.x;
+    double* V = smem;            // V, then L (lower)
+    double* Z = V + R * LD;      // L^-1 (lower)
+    double* dinv = Z + R * LD;   // [R] 1 / L_jj
+    double* dg = dinv + R;       // [R] diagonal of V before the factorisation
+    __shared__ int bad;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < R * R; e += nth) {
+        const int a = e / R, b = e - a * R;
+        double v = 1.0;
+        for (int n = 0; n < p.N; ++n)
+            if (n != p.mode) v *= p.grams[(int64_t)n * R * R + e];
+        V[a * LD + b] = v;
+        Z[a * LD + b] = a == b ? 1.0 : 0.0;
+        if (a == b) dg[a] = v;
+    }
+    __syncthreads();
+    // Cholesky: a pivot below 1e-12 of its original diagonal entry (or not
+    // positive) marks V as singular and stops the update of this mode.
+    for (int j = 0; j < R; ++j) {
+        if (tid == 0) {
+            double d = V[j * LD + j];
+            if (!(d > 1e-12 * dg[j])) {
+                if (!bad) bad = j + 1;
+                d = dg[j] > 0.0 ? dg[j] : 1.0;  // keeps the arithmetic finite; the result is discarded
+            }
+            d = sqrt(d);
+            V[j * LD + j] = d;
+            dinv[j] = 1.0 / d;
+        }
+        __syncthreads();
+        for (int i = j + 1 + tid; i < R; i += nth) V[i * LD + j] *= dinv[j];
+        __syncthreads();
+        const int n = R - j - 1;  // trailing block: rows/cols j+1 .. R-1, lower triangle
+        for (int e = tid; e < n * n; e += nth) {
+            const int i = j + 1 + e / n, k = j + 1 + e % n;
+            if (k <= i) V[i * LD + k] -= V[i * LD + j] * V[k * LD + j];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) *p.info = bad;
+        return;
+    }
+    // Z = L^-1, one column of L at a time: scale row q, then eliminate below it
+    for (int q = 0; q < R; ++q) {
+        for (int c = tid; c <= q; c += nth) Z[q * LD + c] *= dinv[q];
+        __syncthreads();
+        const int n = R - q - 1, w = q + 1;
+        for (int e = tid; e < n * w; e += nth) {
+            const int i = q + 1 + e / w, c = e % w;
+            Z[i * LD + c] -= V[i * LD + q] * Z[q * LD + c];
+        }
+        __syncthreads();
+    }
+    // W = Z^T Z (Z lower triangular: Y_ab = sum_{q >= max(a,b)} Z_qa Z_qb)
+    for (int e = tid; e < R * R; e += nth) {
+        const int a = e / R, b = e - a * R;
+        const int lo = a > b ? a : b;
+        double sum = 0.0;
+        for (int q = lo; q < R; ++q) sum += Z[q * LD + a] * Z[q * LD + b];
+        p.w[e] = (float)sum;
+    }
+    if (tid == 0) *p.info = 0;
+}
+
+// Two passes over the MTTKRP output M (row-major [rows][R]) with the solve's
+// W = V^-1 (fp32), same arithmetic in both:
+//   NORM:  colsq[r] += sum_i ((M W)(i,r))^2                 (nothing stored)
+//   apply: lambda_r = sqrt(colsq[r]); A = M W diag(1/lambda) stored; in the
+//          same pass G += A^T A (of the fp32 values stored) and
+//          ip[r] += sum_i M(i,r) A(i,r).
+// The norms come from the products themselves, so lambda is positive and
+// consistent with the stored factor however ill-conditioned V is.  Both do
+// nothing when the solve reported a singular V.  RP = R rounded up to 8, 16,
+// 32 or 64; a thread computes 4 rows x 4 columns: rows rg, rg + RG, rg + 2 RG,
+// rg + 3 RG of the staged block (consecutive row groups hit different
+// shared-memory banks).
+template <int RP, bool NORM>
+__global__ void __launch_bounds__(256, 2) apply_kernel(const float* __restrict__ M, int64_t rows, AlsParams p,
+                                                       float* __restrict__ A) {
+    constexpr int CT = RP / 4;    // column tiles
+    constexpr int RG = 256 / CT;  // row groups
+    constexpr int ROWS = 4 * RG;  // rows per block iteration
+    constexpr int LD = RP + 4;
+    // W, then the M tile (reused for the A tile); the Gram's block reduction
+    // reuses the same storage once the loop is done
+    constexpr int kFloats = (RP + ROWS) * LD;
+    static_assert(GramAcc<RP>::TILES * 16 * 2 <= kFloats, "reduction does not fit");
+    __shared__ __align__(16) float sm[kFloats];
+    __shared__ double colr[RP];
+    float* w = sm;
+    float* m = sm + RP * LD;
+    double* red = reinterpret_cast<double*>(sm);
+    if (*p.info) return;
+    const int R = p.R;
+    const int tid = threadIdx.x, ct = tid % CT, rg = tid / CT, c0 = ct * 4;
+    for (int e = tid; e < RP; e += blockDim.x) {
+        double scale = 1.0;  // NORM: W as solved; apply: W / lambda (0 for an empty column)
+        if (!NORM) {
+            const double l = e < R ? sqrt(p.colsq[e]) : 0.0;
+            scale = l > 0.0 ? 1.0 / l : 0.0;
+            if (blockIdx.x == 0 && e < R) {
+                p.lambda[e] = (float)l;
+                p.lam64[e] = l;
+            }
+        }
+        colr[e] = scale;
+    }
+    __syncthreads();
+    for (int e = tid; e < RP * LD; e += blockDim.x) {
+        const int k = e / LD, col = e - k * LD;
+        w[e] = (k < R && col < R) ? (float)((double)p.w[k * R + col] * colr[col]) : 0.f;
+    }
+    for (int e = tid; e < ROWS * LD; e += blockDim.x) m[e] = 0.f;  // padding columns stay zero
+    __syncthreads();
+    for (int e = tid; e < RP; e += blockDim.x) colr[e] = 0.0;  // now the per-column block sums
+    GramAcc<RP> gram;
+    if (!NORM) gram.init();
+    float cs[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};  // Kahan: per-column sums
+    for (int64_t base = (int64_t)blockIdx.x * ROWS; base < rows; base += (int64_t)gridDim.x * ROWS) {
+        const int nr = (int)(rows - base < ROWS ? rows - base : ROWS);
+        __syncthreads();
+        stage_rows(M, base, nr, R, m, LD);
+        __syncthreads();
+        unsigned long long acc[4][2];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0ull;
+#pragma unroll 2
+        for (int k = 0; k < RP; k += 4) {
+            float4 a[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(m + (rg + i * RG) * LD + k);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 b = *reinterpret_cast<const float4*>(w + (k + j) * LD + c0);
+                const unsigned long long b01 = pack2(b.x, b.y), b23 = pack2(b.z, b.w);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float av = j == 0 ? a[i].x : j == 1 ? a[i].y : j == 2 ? a[i].z : a[i].w;
+                    const unsigned long long aa = pack2(av, av);
+                    acc[i][0] = ffma2(aa, b01, acc[i][0]);
+                    acc[i][1] = ffma2(aa, b23, acc[i][1]);
+                }
+            }
+        }
+        float v[4][4];
+        float part[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            v[i][0] = lo2(acc[i][0]);
+            v[i][1] = hi2(acc[i][0]);
+            v[i][2] = lo2(acc[i][1]);
+            v[i][3] = hi2(acc[i][1]);
+            if (rg + i * RG < nr) {
+                if (NORM) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) part[q] = fmaf(v[i][q], v[i][q], part[q]);
+                } else {
+                    const float4 mv = *reinterpret_cast<const float4*>(m + (rg + i * RG) * LD + c0);
+                    part[0] = fmaf(mv.x, v[i][0], part[0]);
+                    part[1] = fmaf(mv.y, v[i][1], part[1]);
+                    part[2] = fmaf(mv.z, v[i][2], part[2]);
+                    part[3] = fmaf(mv.w, v[i][3], part[3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float y = part[q] - cc[q];
+            const float t = cs[q] + y;
+            cc[q] = (t - cs[q]) - y;
+            cs[q] = t;
+        }
+        if (NORM) continue;
+        __syncthreads();  // every read of the M tile is done: reuse it for A
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = rg + i * RG;
+            if (row >= nr) continue;
+            *reinterpret_cast<float4*>(m + row * LD + c0) = make_float4(v[i][0], v[i][1], v[i][2], v[i][3]);
+            float* dst = A + (base + row) * R;
+            if ((R & 3) == 0) {
+                if (c0 < R) *reinterpret_cast<float4*>(dst + c0) = make_float4(v[i][0], v[i][1], v[i][2], v[i][3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c0 + q < R) dst[c0 + q] = v[i][q];
+            }
+        }
+        __syncthreads();
+        gram.add(m, nr, LD);
+    }
+    if (!NORM) gram.flush(red, p.ga, R);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (c0 + q < R) atomicAdd(&colr[c0 + q], (double)cs[q] - (double)cc[q]);
+    __syncthreads();
+    double* dst = NORM ? p.colsq : p.ip;
+    for (int e = tid; e < R; e += blockDim.x) atomicAdd(dst + e, colr[e]);
+}
+
+// One block: when the update succeeded, grams[mode] = the new Gram; after the
+// last mode, the fit terms of the stored model.  On a singular V the counters
+// are bumped and the old Gram stays.
+__global__ void __launch_bounds__(256) finish_kernel(AlsParams p) {
+    const int R = p.R, tid = threadIdx.x;
+    __shared__ double red[2][8];
+    const int info = *p.info;
+    if (info == 0) {
+        double* gout = p.grams + (int64_t)p.mode * R * R;
+        for (int e = tid; e < R * R; e += blockDim.x) gout[e] = p.ga[e];
+    } else if (tid == 0) {
+        p.stats[5] += 1.0;
+        if (p.stats[6] == 0.0) p.stats[6] = (double)(p.mode + 1);
+    }
+    if (!p.last) return;
+    if (info != 0) {
+        if (tid == 0)
+            for (int q = 0; q < 5; ++q) p.stats[q] = NAN;
+        return;
+    }
+    __syncthreads();  // the committed Gram is read back below
+    double xy = 0.0, yy = 0.0;
+    for (int e = tid; e < R * R; e += blockDim.x) {
+        const int a = e / R, b = e - a * R;
+        double v = p.lam64[a] * p.lam64[b];
+        for (int n = 0; n < p.N; ++n) v *= p.grams[(int64_t)n * R * R + e];
+        yy += v;
+        if (a == b) xy += p.lam64[a] * p.ip[a];
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int o = 16; o > 0; o >>= 1) {
+        xy += __shfl_xor_sync(0xffffffffu, xy, o);
+        yy += __shfl_xor_sync(0xffffffffu, yy, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = xy;
+        red[1][warp] = yy;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double xs = 0.0, ys = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            xs += red[0][q];
+            ys += red[1][q];
+        }
+        const double xx = p.xnorm2;
+        const double res = xx - 2.0 * xs + ys;
+        const double res_c = res > 0.0 ? res : 0.0;
+        p.stats[0] = xx > 0.0 ? 1.0 - sqrt(res_c) / sqrt(xx) : 0.0;
+        p.stats[1] = res_c;
+        p.stats[2] = xx;
+        p.stats[3] = xs;
+        p.stats[4] = ys;
+    }
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 152;
+    return sms;
+}
+
+int grid_for(int64_t units, int per_block, int blocks_per_sm) {
+    const int64_t cap = (int64_t)sm_count() * (blocks_per_sm > 0 ? blocks_per_sm : 1);
+    int64_t g = (units + per_block - 1) / per_block;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// Blocks of `kernel` (256 threads, static shared memory) resident on one SM.
+template <class K>
+int resident(K kernel) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 256, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+int padded_rank(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
+
+}  // namespace
+
+int als_max_rank() { return kAlsMaxRank; }
+
+int launch_gram(const float* A, int64_t rows, int R, double* G, void* stream, int* launched) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (R < 1 || R > kAlsMaxRank) return (int)cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * R * R, st);
+    if (e != cudaSuccess) return (int)e;
+    if (rows <= 0) return 0;
+#define AMPED_GRAM_CASE(RP)                                                                                \
+    case RP:                                                                                               \
+        gram_kernel<RP><<<grid_for(rows, GramTile<RP>::ROWS, resident(gram_kernel<RP>)), 256, 0, st>>>(A, rows, R, G); \
+        break;
+    switch (padded_rank(R)) {
+        AMPED_GRAM_CASE(8)
+        AMPED_GRAM_CASE(16)
+        AMPED_GRAM_CASE(32)
+        default: AMPED_GRAM_CASE(64)
+    }
+#undef AMPED_GRAM_CASE
+    ++*launched;
+    return (int)cudaGetLastError();
+}
+
+int launch_als_solve(const AlsParams& p, void* stream, int* launched) {
+    if (p.R < 1 || p.R > kAlsMaxRank) return (int)cudaErrorInvalidValue;
+    const size_t bytes = sizeof(double) * ((size_t)2 * p.R * (p.R + 1) + 2 * (size_t)p.R);
+    const cudaError_t attr = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (attr != cudaSuccess) return (int)attr;
+    solve_kernel<<<1, 256, bytes, static_cast<cudaStream_t>(stream)>>>(p);
+    ++*launched;
+    return (int)cudaGetLastError();
+}
+
+template <int RP>
+static void apply_passes(const AlsParams& p, const float* M, int64_t rows, float* A, cudaStream_t st, int* launched) {
+    const int rows_per_block = 4 * (256 / (RP / 4));
+    apply_kernel<RP, true><<<grid_for(rows, rows_per_block, resident(apply_kernel<RP, true>)), 256, 0, st>>>(
+        M, rows, p, A);
+    apply_kernel<RP, false><<<grid_for(rows, rows_per_block, resident(apply_kernel<RP, false>)), 256, 0, st>>>(
+        M, rows, p, A);
+    *launched += 2;
+}
+
+int launch_als_apply(const AlsParams& p, const float* M, int64_t rows, float* A, void* stream, int* launched) {
+    if (p.R < 1 || p.R > kAlsMaxRank) return (int)cudaErrorInvalidValue;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int R = p.R;
+    // colsq [R], ga [R][R], ip [R] are contiguous in the workspace
+    cudaError_t e = cudaMemsetAsync(p.colsq, 0, sizeof(double) * ((size_t)R * R + 2 * R), st);
+    if (e != cudaSuccess) return (int)e;
+    if (rows > 0) {
+        switch (padded_rank(R)) {
+            case 8: apply_passes<8>(p, M, rows, A, st, launched); break;
+            case 16: apply_passes<16>(p, M, rows, A, st, launched); break;
+            case 32: apply_passes<32>(p, M, rows, A, st, launched); break;
+            default: apply_passes<64>(p, M, rows, A, st, launched); break;
+        }
+    }
+    finish_kernel<<<1, 256, 0, st>>>(p);
+    ++*launched;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace amped

@@ -105,6 +105,13 @@ void gather_values(const HostMode& hm, const float* vals, float* dst, int thread
 // Caller-order column: dst[k] = idx[k][mode].
 void caller_column(int64_t nnz, int nmodes, const int32_t* idx, int mode, int32_t* dst, int threads);
 
+// ||X||^2 with repeated coordinates summed into one entry, from the copy
+// ordered by order_mode (before classify_rows): runs of equal row (and equal
+// `inner` coordinate when inner >= 0) are sorted by the full coordinate so
+// repeats become adjacent.  fp64, the same result for any thread count.
+// Returns a negative value on allocation failure.
+double norm2_merged(const HostMode& hm, int nmodes, const int32_t* idx, const float* vals, int inner, int threads);
+
 // ---------------------------------------------------------------------------
 // Device side.
 // ---------------------------------------------------------------------------
@@ -146,6 +153,29 @@ struct SampleParams {
     float* m;                             // [nnz] (+ slack for the vector store)
     int32_t nnz, R, nmodes;
 };
+
+// One CP-ALS mode update (als.cu).
+struct AlsParams {
+    double* grams;       // [N][R][R] Grams of the current factors; row `mode` is replaced on success
+    float* w;            // [R][R] V^-1, fp32 (workspace)
+    float* lambda;       // [R] column norms of the unnormalised update (caller's buffer)
+    double* lam64;       // [R] the same norms in fp64 (workspace)
+    double* colsq;       // [R] squared column norms of M V^-1, then (contiguous) ...
+    double* ga;          // [R][R] ... the Gram of the stored update, then ...
+    double* ip;          // [R] ... sum_i M(i,r) A(i,r) of the stored update
+    int* info;           // 0, or the first failed Cholesky pivot + 1
+    double* stats;       // [8] fit terms (written after the last mode), failure counters
+    double xnorm2;       // ||X||^2
+    int32_t N, mode, R, last;
+};
+int als_max_rank();
+// G = A^T A (fp64; G is zeroed first) of a row-major [rows][R] fp32 matrix.
+int launch_gram(const float* A, int64_t rows, int R, double* G, void* stream, int* launched);
+// Cholesky solve: w = V^-1, info.
+int launch_als_solve(const AlsParams& p, void* stream, int* launched);
+// Norm pass and apply pass (A = M W diag(1/lambda), its Gram, ip) unless the
+// solve failed, then the commit of the Gram and, after the last mode, the fit.
+int launch_als_apply(const AlsParams& p, const float* M, int64_t rows, float* A, void* stream, int* launched);
 
 // Split-row combine launcher (combine.cu).  Returns a cudaError_t value as
 // int, counts the kernels it launched, never synchronises.

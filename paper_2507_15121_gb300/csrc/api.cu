@@ -126,6 +126,12 @@ struct amped_tensor {
     size_t stage_fac_bytes[AMPED_MAX_MODES] = {};
     float* stage_out[AMPED_MAX_MODES] = {};
     size_t stage_out_bytes[AMPED_MAX_MODES] = {};
+    double xnorm2 = 0.0;        // ||X||^2, repeated coordinates summed
+    float* als_m = nullptr;     // CP-ALS: MTTKRP output [max dim][als_rcap]
+    double* als_gm = nullptr;   // CP-ALS: column sums [R], the update's Gram [R][R], ip [R], lambda [R]
+    float* als_w = nullptr;     // CP-ALS: solve output [R][R]
+    int* als_info = nullptr;    // CP-ALS: solve status
+    int als_rcap = 0;
     std::vector<void*> allocs;
 
     cudaError_t dalloc(void** p, size_t bytes) {
@@ -179,6 +185,33 @@ amped_status ensure_scratch(amped_tensor* t, int R) {
         cudaSuccess)
         return cuda_fail(e, "scratch allocation");
     t->rcap = rc;
+    return AMPED_OK;
+}
+
+// CP-ALS workspace for rank R: the MTTKRP output of the largest mode, its Gram,
+// the solve output and status.
+amped_status ensure_als(amped_tensor* t, int R) {
+    if (R <= t->als_rcap) return AMPED_OK;
+    int64_t rows = 0;
+    for (int n = 0; n < t->N; ++n) rows = std::max<int64_t>(rows, t->dims[n]);
+    cudaDeviceSynchronize();  // the old workspace may still be in use on any stream
+    t->dfree(t->als_m);
+    t->dfree(t->als_gm);
+    t->dfree(t->als_w);
+    t->dfree(t->als_info);
+    t->als_m = nullptr;
+    t->als_gm = nullptr;
+    t->als_w = nullptr;
+    t->als_info = nullptr;
+    t->als_rcap = 0;
+    cudaError_t e;
+    if ((e = t->dalloc(reinterpret_cast<void**>(&t->als_m), (size_t)rows * R * sizeof(float))) != cudaSuccess ||
+        (e = t->dalloc(reinterpret_cast<void**>(&t->als_gm), ((size_t)R * R + 3 * R) * sizeof(double))) !=
+            cudaSuccess ||
+        (e = t->dalloc(reinterpret_cast<void**>(&t->als_w), (size_t)R * R * sizeof(float))) != cudaSuccess ||
+        (e = t->dalloc(reinterpret_cast<void**>(&t->als_info), 16)) != cudaSuccess)
+        return cuda_fail(e, "CP-ALS workspace allocation");
+    t->als_rcap = R;
     return AMPED_OK;
 }
 
@@ -360,8 +393,13 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
     cudaError_t e;
     for (int mode = 0; mode < nmodes; ++mode) {
         HostMode hm;
-        if (!order_mode(nnz, nmodes, dims, idx, mode, inner_sort, threads, hm) ||
-            !classify_rows(hm, short_thr, threads) || !cut_segments(hm, items))
+        if (!order_mode(nnz, nmodes, dims, idx, mode, inner_sort, threads, hm))
+            return bail(fail(AMPED_ERR_OOM, "host allocation failed in the reorder of mode %d", mode));
+        if (mode == 0) {
+            t->xnorm2 = norm2_merged(hm, nmodes, idx, vals, inner_sort ? inner_mode(nmodes, dims, 0) : -1, threads);
+            if (t->xnorm2 < 0.0) return bail(fail(AMPED_ERR_OOM, "host allocation failed computing the tensor norm"));
+        }
+        if (!classify_rows(hm, short_thr, threads) || !cut_segments(hm, items))
             return bail(fail(AMPED_ERR_OOM, "host allocation failed in the reorder of mode %d", mode));
         DevMode& dm = t->m[mode];
         dm.I = hm.I;
@@ -650,6 +688,68 @@ amped_status amped_cp_completion_grad(amped_tensor_t t, const void* const* facto
         // the loss is accumulated once, in the pass over mode 0
         s = run_mode(t, n, factors, fdtype, R, vec, grads[n], nullptr, st, true, n == 0 ? loss : nullptr);
         if (s != AMPED_OK) return s;
+    }
+    return AMPED_OK;
+}
+
+amped_status amped_tensor_norm2(amped_tensor_t t, double* norm2) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (!norm2) return fail(AMPED_ERR_INVALID, "norm2 is NULL");
+    *norm2 = t->xnorm2;
+    return AMPED_OK;
+}
+
+amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, float* lambda, double* grams,
+                                double* stats, int flags, void* stream) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (!factors || !lambda || !grams || !stats)
+        return fail(AMPED_ERR_INVALID, "factors, lambda, grams or stats is NULL");
+    if (flags & ~AMPED_ALS_INIT) return fail(AMPED_ERR_INVALID, "unknown flags 0x%x", flags);
+    if (R < 1) return fail(AMPED_ERR_INVALID, "rank R=%d must be >= 1", R);
+    if (R > als_max_rank()) return fail(AMPED_ERR_UNSUPPORTED, "CP-ALS is built for ranks up to %d", als_max_rank());
+    if (t->N < 2 || t->N - 1 > 4) return fail(AMPED_ERR_UNSUPPORTED, "CP-ALS is built for 2 to 5 modes");
+    const void* cf[AMPED_MAX_MODES];
+    for (int n = 0; n < t->N; ++n) cf[n] = factors[n];
+    int vec = 0;
+    amped_status s = check_call(t, cf, AMPED_F32, R, -1, &vec);
+    if (s != AMPED_OK) return s;
+    for (int n = 0; n < t->N; ++n)
+        if (!aligned(factors[n], 16)) return fail(AMPED_ERR_INVALID, "factor %d is not 16-byte aligned", n);
+    if (!aligned(grams, 8) || !aligned(stats, 8) || !aligned(lambda, 4))
+        return fail(AMPED_ERR_INVALID, "lambda, grams or stats is misaligned");
+    if ((s = ensure_als(t, R)) != AMPED_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int launched = 0, rc = 0;
+    if (flags & AMPED_ALS_INIT)
+        for (int n = 0; n < t->N && rc == 0; ++n) rc = launch_gram(factors[n], t->dims[n], R, grams + (size_t)n * R * R, st, &launched);
+    if (rc == 0) rc = (int)cudaMemsetAsync(stats + 5, 0, 2 * sizeof(double), st);
+    g_launches += launched;
+    if (rc != 0) return cuda_fail((cudaError_t)rc, "CP-ALS initial Grams");
+    for (int m = 0; m < t->N; ++m) {
+        s = run_mode(t, m, cf, AMPED_F32, R, vec, t->als_m, nullptr, st);
+        if (s != AMPED_OK) return s;
+        launched = 0;
+        AlsParams p{};
+        p.grams = grams;
+        p.colsq = t->als_gm;
+        p.ga = p.colsq + R;
+        p.ip = p.ga + (size_t)R * R;
+        p.lam64 = p.ip + R;
+        p.w = t->als_w;
+        p.lambda = lambda;
+        p.info = t->als_info;
+        p.stats = stats;
+        p.xnorm2 = t->xnorm2;
+        p.N = t->N;
+        p.mode = m;
+        p.R = R;
+        p.last = m == t->N - 1;
+        rc = launch_als_solve(p, st, &launched);
+        if (rc == 0) rc = launch_als_apply(p, t->als_m, t->dims[m], factors[m], st, &launched);
+        g_launches += launched;
+        if (rc != 0) return cuda_fail((cudaError_t)rc, "CP-ALS kernel launch");
     }
     return AMPED_OK;
 }

@@ -321,4 +321,76 @@ void caller_column(int64_t nnz, int nmodes, const int32_t* idx, int mode, int32_
     for (int64_t k = 0; k < nnz; ++k) dst[k] = idx[k * nmodes + mode];
 }
 
+double norm2_merged(const HostMode& hm, int nmodes, const int32_t* idx, const float* vals, int inner, int threads) {
+    const int T = nthreads(threads);
+    constexpr int64_t kRowsPerChunk = 4096;
+    const int64_t nch = (hm.I + kRowsPerChunk - 1) / kRowsPerChunk;
+    std::vector<double> part;
+    try {
+        part.assign((size_t)nch, 0.0);
+    } catch (...) {
+        return -1.0;
+    }
+    auto same = [&](int32_t x, int32_t y) {
+        for (int n = 0; n < nmodes; ++n)
+            if (idx[(int64_t)x * nmodes + n] != idx[(int64_t)y * nmodes + n]) return false;
+        return true;
+    };
+    auto less = [&](int32_t x, int32_t y) {
+        for (int n = 0; n < nmodes; ++n) {
+            const int32_t a = idx[(int64_t)x * nmodes + n], b = idx[(int64_t)y * nmodes + n];
+            if (a != b) return a < b;
+        }
+        return false;
+    };
+    bool failed = false;
+#pragma omp parallel num_threads(T)
+    {
+        std::vector<int32_t> run;
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t c = 0; c < nch; ++c) {
+            double s = 0.0;
+            const int64_t i_end = std::min<int64_t>(hm.I, (c + 1) * kRowsPerChunk);
+            for (int64_t i = c * kRowsPerChunk; i < i_end; ++i) {
+                int64_t a = hm.rowptr[(size_t)i];
+                const int64_t b = hm.rowptr[(size_t)i + 1];
+                while (a < b) {
+                    int64_t e = b;
+                    if (inner >= 0) {
+                        const int32_t key = idx[(int64_t)hm.perm[(size_t)a] * nmodes + inner];
+                        e = a + 1;
+                        while (e < b && idx[(int64_t)hm.perm[(size_t)e] * nmodes + inner] == key) ++e;
+                    }
+                    if (e - a == 1) {
+                        const double v = vals[hm.perm[(size_t)a]];
+                        s += v * v;
+                    } else {
+                        try {
+                            run.assign(hm.perm.p + a, hm.perm.p + e);
+                        } catch (...) {
+#pragma omp atomic write
+                            failed = true;
+                            break;
+                        }
+                        std::stable_sort(run.begin(), run.end(), less);  // equal coordinates keep copy order
+                        for (size_t j = 0; j < run.size();) {
+                            double v = 0.0;
+                            size_t q = j;
+                            while (q < run.size() && same(run[q], run[j])) v += vals[run[q++]];
+                            s += v * v;
+                            j = q;
+                        }
+                    }
+                    a = e;
+                }
+            }
+            part[(size_t)c] = s;
+        }
+    }
+    if (failed) return -1.0;
+    double total = 0.0;
+    for (double v : part) total += v;  // fixed chunk order
+    return total;
+}
+
 }  // namespace amped

@@ -1,0 +1,192 @@
+"""GPU parity of the CP-ALS sweep (amped_cp_als_sweep) against the FP64 ALS
+oracle (oracle/als.py), through the C ABI.
+
+The GPU keeps fp32 factors and an fp32 MTTKRP; the Grams, the Cholesky solve
+and the fit terms are fp64; the update M V^-1 is applied in fp32.  Error
+budget of one mode update, from its own inputs:
+  * M carries the fp32 MTTKRP error, at most EPS_M = 1e-5 relative per row;
+  * the R-term fp32 dot products of M W add about R * 2^-24;
+  * both reach the least-squares solution amplified by at most cond(V).
+So mode n is checked against the oracle's update of the SAME inputs (the
+GPU's already-updated factors before n, the starting factors after n) with
+the bar 4 cond_n (EPS_M + R 2^-24) on unit-norm columns.  The Gram the GPU
+keeps for each mode is checked against the Gram of the fp32 factor it
+stored (no conditioning involved), and the fit terms against the oracle's
+evaluation of the GPU's own model: ||X - X^||^2 = ||X||^2 - 2<X, X^> +
+||X^||^2 with each term within 1e-5 (||X||^2 + ||X^||^2) (the scale that
+bounds |<X, X^>|), and so the residual.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import als
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2507_15121_gb300 as amped  # noqa: E402
+
+EPS_M = 1e-5
+TERM_BAR = 1e-5
+
+
+def to_dev(arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda() for a in arrs]
+
+
+def col_error(gpu, ref):
+    """max over columns of max_i |g - o| / max_i |o|."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = np.abs(ref).max(axis=0)
+    den[den == 0] = 1.0
+    return float((np.abs(gpu - ref).max(axis=0) / den).max())
+
+
+def gpu_sweeps(dims, idx, vals, F, sweeps=1):
+    t = amped.Tensor(dims, idx, vals)
+    Fd = to_dev(F)
+    R = F[0].shape[1]
+    lam = torch.empty(R, device="cuda")
+    grams = torch.empty((len(dims), R, R), dtype=torch.float64, device="cuda")
+    stats = torch.zeros(8, dtype=torch.float64, device="cuda")
+    hist = []
+    for s in range(sweeps):
+        t.cp_als_sweep(Fd, lam, grams, stats, init=(s == 0))
+        torch.cuda.synchronize()
+        hist.append(stats.cpu().numpy().copy())
+    out = [f.cpu().numpy() for f in Fd], lam.cpu().numpy().astype(np.float64), grams.cpu().numpy(), hist, t.norm2()
+    t.close()
+    return out
+
+
+def check_fit_terms(dims, idx, vals, A, lam, st):
+    """stats of a sweep against the oracle's evaluation of the same (GPU) model."""
+    xx, xy, yy = als.fit_terms(dims, idx, vals, [a.astype(np.float64) for a in A], lam)
+    assert st[2] == pytest.approx(xx, rel=1e-12)
+    assert abs(st[3] - xy) <= TERM_BAR * (xx + yy), (st[3], xy)  # |<X, X^>| <= (||X||^2 + ||X^||^2) / 2
+    assert abs(st[4] - yy) <= TERM_BAR * (xx + yy), (st[4], yy)
+    res = max(xx - 2 * xy + yy, 0.0)
+    assert abs(st[1] - res) <= TERM_BAR * (xx + yy), (st[1], res)
+    return 1.0 - np.sqrt(res) / np.sqrt(xx)
+
+
+def workload(name, scale=None):
+    w = synth.WORKLOADS[name]
+    if scale is not None:
+        w = w.scaled(scale)
+    return w, synth.make(w)
+
+
+CASES = [("uniform3", None, 16), ("zipf3", 0.0005, 32), ("zipf4", 0.0001, 32), ("zipf5", 0.0002, 16),
+         ("zipf3", 0.0002, 8), ("zipf3", 0.0002, 20), ("zipf3", 0.0002, 40), ("zipf3", 0.0002, 64),
+         ("zipf3", 0.0002, 3)]
+
+
+@pytest.mark.parametrize("name,scale,R", CASES)
+def test_one_sweep_matches_oracle(name, scale, R):
+    w, c = workload(name, scale)
+    F = synth.factors(c.dims, R, w.seed)
+    Ag, lam_g, grams_g, hist, n2 = gpu_sweeps(c.dims, c.idx, c.vals, F)
+    N = c.nmodes
+    for n in range(N):
+        # the inputs mode n saw: updated factors before it, starting factors after it
+        inp = [Ag[k].astype(np.float64) if k < n else F[k].astype(np.float64) for k in range(N)]
+        V = als.hadamard_others([als.gram(a) for a in inp], n)
+        bar = 4 * np.linalg.cond(V) * (EPS_M + R * 2.0 ** -24)
+        A_o, lam_o = als.update_mode(c.dims, c.idx, c.vals, inp, n)
+        err = col_error(Ag[n], A_o)
+        assert err <= bar, (n, err, bar)
+        np.testing.assert_allclose(np.linalg.norm(Ag[n].astype(np.float64), axis=0), 1.0, atol=max(1e-5, bar))
+        G = als.gram(Ag[n])  # the Gram of what was stored
+        assert np.abs(grams_g[n] - G).max() <= 1e-6 * np.abs(G).max(), n
+        if n == N - 1:
+            assert np.abs(lam_g - lam_o).max() <= bar * np.abs(lam_o).max()
+    st = hist[0]
+    check_fit_terms(c.dims, c.idx, c.vals, Ag, lam_g, st)
+    assert st[5] == 0 and st[6] == 0
+    assert abs(n2 - als.norm2(c.idx, c.vals)) <= 1e-12 * n2
+    assert st[2] == n2
+
+
+def test_sweeps_track_the_oracle_fit():
+    w, c = workload("zipf3", 0.0005)
+    F = synth.factors(c.dims, 16, w.seed)
+    Ag, lam_g, _, hist, _ = gpu_sweeps(c.dims, c.idx, c.vals, F, sweeps=6)
+    _, _, fits_o = als.run(c.dims, c.idx, c.vals, F, 6)
+    got = np.array([s[0] for s in hist])
+    assert np.all(np.abs(got - np.array(fits_o)) <= 1e-3), (got, fits_o)
+    assert np.all(np.diff(got) >= -1e-5)  # ALS does not increase the residual
+    check_fit_terms(c.dims, c.idx, c.vals, Ag, lam_g, hist[-1])
+
+
+def block_low_rank(R, block, seed):
+    """Sparse tensor of exact rank R: R dense rank-1 blocks on disjoint coordinate ranges."""
+    rng = np.random.default_rng(seed)
+    dims = (R * block[0], R * block[1], R * block[2])
+    idx, vals = [], []
+    B = [np.zeros((d, R)) for d in dims]
+    for r in range(R):
+        vecs = [rng.uniform(0.5, 1.5, b) for b in block]
+        for n in range(3):
+            B[n][r * block[n]:(r + 1) * block[n], r] = vecs[n]
+        g = np.stack(np.meshgrid(*[np.arange(b) for b in block], indexing="ij"), -1).reshape(-1, 3)
+        idx.append(g + np.array([r * b for b in block]))
+        vals.append(vecs[0][g[:, 0]] * vecs[1][g[:, 1]] * vecs[2][g[:, 2]])
+    return dims, np.concatenate(idx).astype(np.int32), np.concatenate(vals).astype(np.float32), B
+
+
+def test_exact_low_rank_sparse_tensor_is_recovered():
+    dims, idx, vals, B = block_low_rank(6, (20, 15, 10), 3)
+    rng = np.random.default_rng(4)
+    F = [(b + 0.05 * rng.uniform(0, 1, b.shape)).astype(np.float32) for b in B]  # start near the truth
+    Ag, lam_g, _, hist, _ = gpu_sweeps(dims, idx, vals, F, sweeps=30)
+    # the fit of the stored model, evaluated by the oracle in fp64: fp32 factors reach ~1e-7
+    true_fit = als.fit(dims, idx, vals, [a.astype(np.float64) for a in Ag], lam_g)
+    assert true_fit > 1 - 1e-5, true_fit
+    # the library's own fit is the fp64 expansion of fp32-accurate terms: near a perfect fit its
+    # resolution is sqrt(TERM_BAR * (||X||^2 + ||X^||^2)) / ||X||
+    assert hist[-1][0] > 1 - np.sqrt(2 * TERM_BAR), hist[-1][0]
+    check_fit_terms(dims, idx, vals, Ag, lam_g, hist[-1])
+
+
+def test_singular_normal_equations_are_reported():
+    w, c = workload("zipf3", 0.0002)
+    R = 4
+    F = synth.factors(c.dims, R, w.seed)
+    for n in (1, 2):  # two equal columns in every other factor make V singular for mode 0
+        F[n][:, 1] = F[n][:, 0]
+    t = amped.Tensor(c.dims, c.idx, c.vals)
+    Fd = to_dev(F)
+    before = Fd[0].clone()
+    lam = torch.empty(R, device="cuda")
+    grams = torch.empty((3, R, R), dtype=torch.float64, device="cuda")
+    stats = torch.zeros(8, dtype=torch.float64, device="cuda")
+    t.cp_als_sweep(Fd, lam, grams, stats, init=True)
+    torch.cuda.synchronize()
+    st = stats.cpu().numpy()
+    assert st[5] >= 1 and st[6] == 1  # mode 0 failed first
+    assert torch.equal(Fd[0], before)  # its factor was left alone
+    with pytest.raises(amped.AmpedError):
+        t.cp_als(to_dev(F), sweeps=2)
+    t.close()
+
+
+def test_argument_errors():
+    w, c = workload("zipf3", 0.0002)
+    t = amped.Tensor(c.dims, c.idx, c.vals)
+    F = to_dev(synth.factors(c.dims, 72, w.seed))
+    lam = torch.empty(72, device="cuda")
+    grams = torch.empty((3, 72, 72), dtype=torch.float64, device="cuda")
+    stats = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(amped.AmpedError) as e:
+        t.cp_als_sweep(F, lam, grams, stats, init=True)
+    assert e.value.status == amped._lib.ERR_UNSUPPORTED
+    Fb = [f[:, :32].contiguous().to(torch.bfloat16) for f in F]
+    with pytest.raises(ValueError):
+        t.cp_als_sweep(Fb, lam[:32].contiguous(), grams[:, :32, :32].contiguous(), stats, init=True)
+    with pytest.raises(ValueError):  # wrong Gram shape
+        t.cp_als_sweep([f[:, :32].contiguous() for f in F], lam[:32].contiguous(), grams, stats)
+    t.close()
