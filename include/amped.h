@@ -176,27 +176,38 @@ amped_status amped_tensor_norm2(amped_tensor_t t, double* norm2);
  * mode-wise MTTKRPs of Eq. 1 in turn; the least-squares update after each MTTKRP is the standard
  * CP-ALS normal-equation step, which the paper does not spell out).  For d = 0 .. N-1, each step
  * seeing the factors updated before it:
- *   M      = MTTKRP_d(X; A_n, n != d)                           (amped_mttkrp, fp32)
- *   V      = Hadamard product over n != d of grams[n]           (fp64)
- *   B      = M V^-1                                             (fp64 Cholesky of V; fp32 apply)
- *   lambda = column 2-norms of B;  A_d = B with unit-norm columns (a zero column stays zero)
- *   grams[d] = A_d^T A_d                                        (fp64)
- * then the fit of the model X^ = [[lambda; A_0, ..., A_{N-1}]]:
+ *   M        = MTTKRP_d(X; A_n, n != d)                         (amped_mttkrp, fp32)
+ *   V        = Hadamard product over n != d of grams[n]         (fp64)
+ *   A_d      = M V^-1                                           (fp64 Cholesky of V; fp32 apply)
+ *   grams[d] = A_d^T A_d of the stored fp32 values              (fp64)
+ * The columns are NOT normalised between modes: least-squares updates are covariant under column
+ * scaling, so the models [[A_0, ..., A_{N-1}]] equal those of the per-step normalised algorithm.
+ * Call amped_cp_als_normalize for unit-norm factors and lambda.  After the sweep, for the model
+ * X^ = [[A_0, ..., A_{N-1}]]:
  *   stats[0] = 1 - ||X - X^|| / ||X||        stats[1] = ||X - X^||^2 (clamped at 0)
  *   stats[2] = ||X||^2                       stats[3] = <X, X^>      stats[4] = ||X^||^2
- *   stats[5] = modes whose V was singular in this sweep (their factor, Gram and lambda are left
+ *   stats[5] = modes whose V was singular in this sweep (their factor and Gram are left
  *              unchanged; a singular last mode sets stats[0..4] to NaN)
  *   stats[6] = first such mode + 1, or 0
  * factors: host array of N device pointers [dims[n]][R] fp32, 16-byte aligned (32-byte when R is
  *          a multiple of 8), updated in place.
- * lambda:  device [R] fp32, written.   grams: device [N][R][R] fp64; on entry the Grams of the
- * factors (or pass AMPED_ALS_INIT to compute them), on return those of the updated factors.
+ * grams:   device [N][R][R] fp64; on entry the Grams of the factors (or pass AMPED_ALS_INIT to
+ *          compute them), on return those of the updated factors.
  * stats:   device [8] fp64.  1 <= R <= 64 (R > 32 a multiple of 8); 2 to 5 modes.
- * The MTTKRP output, its Gram and the solve's result live in workspace the handle allocates on
- * first use (dims_max x R fp32).  Asynchronous: read stats after synchronising the stream.
+ * The MTTKRP output and the solve's result live in workspace the handle allocates on first use
+ * (dims_max x R fp32).  Asynchronous: read stats after synchronising the stream.
  */
-amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, float* lambda, double* grams,
-                                double* stats, int flags, void* stream);
+amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, double* grams, double* stats,
+                                int flags, void* stream);
+
+/*
+ * Normalised form of a CP model [[A_0, ..., A_{N-1}]] = [[lambda; B_0, ..., B_{N-1}]]: every
+ * factor's columns scaled to unit 2-norm in place (a zero column stays zero), lambda_r = product
+ * over n of the column norms (device [R] fp32), and grams (device [N][R][R] fp64, the Grams of the
+ * factors on entry) rescaled to the unit-norm factors.  One pass over every factor.
+ */
+amped_status amped_cp_als_normalize(amped_tensor_t t, float* const* factors, int R, double* grams, float* lambda,
+                                    void* stream);
 
 /* Sizes of a mode's plan (amped_plan_mode). */
 typedef struct {

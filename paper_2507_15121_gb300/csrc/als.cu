@@ -2,35 +2,31 @@
 //
 // CP decomposition by alternating least squares (Sec. 2.1: ALS performs the
 // mode-wise MTTKRPs of Eq. 1 in turn, iteratively).  After the mode-d MTTKRP
-// M = X_(d) (Khatri-Rao of the other factors) the factor is the least-squares
-// solution A_d = M V^-1 with V the Hadamard product of the other factors'
-// Gram matrices; its columns are then scaled to unit norm and the norms kept
-// as lambda.  Per mode the library runs:
+// M = X_(d) (Khatri-Rao of the other factors) the factor becomes the
+// least-squares solution A_d = M V^-1, V the Hadamard product of the other
+// factors' Gram matrices.  Per mode the library runs:
 //
-//   solve_kernel   one block, fp64:            V = Hadamard of the other Grams,
-//                                              Cholesky V = L L^T, W = V^-1
-//                                              (written as fp32)
-//   apply_kernel   norm pass: lambda_r = ||(M W)_r||, from the same fp32
-//                  products the apply pass uses (nothing stored);
-//                  apply pass: A_d = M W diag(1/lambda) stored, fp32, 4x4
-//                  register tiles (packed f32x2 FMA); the same pass
-//                  accumulates the Gram of the stored A_d and
-//                  ip_r = sum_i M(i,r) A_d(i,r)
+//   solve_kernel   one block, fp64: V = Hadamard of the other Grams,
+//                  Cholesky V = L L^T, W = V^-1 (written as fp32)
+//   apply_kernel   A_d = M W stored (fp32, 4x4 register tiles, packed f32x2
+//                  FMA); the same pass accumulates the Gram of the stored
+//                  A_d and ip_r = sum_i M(i,r) A_d(i,r)
 //   finish_kernel  one block: commits the new Gram; after the last mode, the fit
 //   gram_kernel    A^T A of the starting factors (first sweep only)
+//   normalize      on request: unit-norm columns, lambda = product of the norms
 //
-// Sums: fp32 over a tile, compensated (Kahan) fp32 across tiles, fp64 across
-// blocks.  lambda is never derived from a quadratic form in V^-1 (which
-// cancels catastrophically when V is ill-conditioned, as it is for the small
-// modes of power-law tensors).
-//
-// The fit is that of the model actually stored, [[lambda; A_0..A_{N-1}]]:
-//   <X, X^>  = sum_r lambda_r ip_r             (MTTKRP identity, last mode)
-//   ||X^||^2 = sum_{r,s} lambda_r lambda_s prod_n G_n(r,s)
-// with every G_n the Gram of the stored fp32 factor.  The closed forms that
-// hold at the exact least-squares optimum (<X, X^> = tr(Gm V^-1)) are not
-// used: they amplify the fp32 rounding of M by cond(V).
-// Ranks up to kAlsMaxRank; every loop over R is bounded by it.
+// The factors are not normalised between modes.  Least-squares updates are
+// covariant under column scaling (scaling a column of one factor scales the
+// matching column of the next update inversely), so the sequence of models
+// [[A_0, ..., A_{N-1}]] equals that of the per-step normalised algorithm; the
+// Gram of every factor is the exact Gram of its stored values, so V stays
+// consistent with what the MTTKRP reads.  The fit is that of the stored model:
+//   <X, X^>  = sum_r ip_r                      (MTTKRP identity, last mode)
+//   ||X^||^2 = sum_{r,s} prod_n G_n(r,s)
+// Neither is derived from a quadratic form in V^-1, which cancels
+// catastrophically when V is ill-conditioned (as it is for the small modes of
+// power-law tensors).  Sums: fp32 over a tile, compensated (Kahan) fp32
+// across tiles, fp64 across blocks.  Ranks up to kAlsMaxRank.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -289,19 +285,13 @@ __global__ void __launch_bounds__(256) solve_kernel(AlsParams p) {
     if (tid == 0) *p.info = 0;
 }
 
-// Two passes over the MTTKRP output M (row-major [rows][R]) with the solve's
-// W = V^-1 (fp32), same arithmetic in both:
-//   NORM:  colsq[r] += sum_i ((M W)(i,r))^2                 (nothing stored)
-//   apply: lambda_r = sqrt(colsq[r]); A = M W diag(1/lambda) stored; in the
-//          same pass G += A^T A (of the fp32 values stored) and
-//          ip[r] += sum_i M(i,r) A(i,r).
-// The norms come from the products themselves, so lambda is positive and
-// consistent with the stored factor however ill-conditioned V is.  Both do
-// nothing when the solve reported a singular V.  RP = R rounded up to 8, 16,
-// 32 or 64; a thread computes 4 rows x 4 columns: rows rg, rg + RG, rg + 2 RG,
-// rg + 3 RG of the staged block (consecutive row groups hit different
-// shared-memory banks).
-template <int RP, bool NORM>
+// A = M W for the MTTKRP output M (row-major [rows][R]) and the solve's
+// W = V^-1 (fp32), stored; in the same pass ga += A^T A (of the fp32 values
+// stored) and ip[r] += sum_i M(i,r) A(i,r).  Does nothing when the solve
+// reported a singular V.  RP = R rounded up to 8, 16, 32 or 64; a thread
+// computes 4 rows x 4 columns: rows rg, rg + RG, rg + 2 RG, rg + 3 RG of the
+// staged block (consecutive row groups hit different shared-memory banks).
+template <int RP>
 __global__ void __launch_bounds__(256, 2) apply_kernel(const float* __restrict__ M, int64_t rows, AlsParams p,
                                                        float* __restrict__ A) {
     constexpr int CT = RP / 4;    // column tiles
@@ -320,28 +310,14 @@ __global__ void __launch_bounds__(256, 2) apply_kernel(const float* __restrict__
     if (*p.info) return;
     const int R = p.R;
     const int tid = threadIdx.x, ct = tid % CT, rg = tid / CT, c0 = ct * 4;
-    for (int e = tid; e < RP; e += blockDim.x) {
-        double scale = 1.0;  // NORM: W as solved; apply: W / lambda (0 for an empty column)
-        if (!NORM) {
-            const double l = e < R ? sqrt(p.colsq[e]) : 0.0;
-            scale = l > 0.0 ? 1.0 / l : 0.0;
-            if (blockIdx.x == 0 && e < R) {
-                p.lambda[e] = (float)l;
-                p.lam64[e] = l;
-            }
-        }
-        colr[e] = scale;
-    }
-    __syncthreads();
     for (int e = tid; e < RP * LD; e += blockDim.x) {
         const int k = e / LD, col = e - k * LD;
-        w[e] = (k < R && col < R) ? (float)((double)p.w[k * R + col] * colr[col]) : 0.f;
+        w[e] = (k < R && col < R) ? p.w[k * R + col] : 0.f;
     }
     for (int e = tid; e < ROWS * LD; e += blockDim.x) m[e] = 0.f;  // padding columns stay zero
-    __syncthreads();
-    for (int e = tid; e < RP; e += blockDim.x) colr[e] = 0.0;  // now the per-column block sums
+    for (int e = tid; e < RP; e += blockDim.x) colr[e] = 0.0;   // per-column block sums of ip
     GramAcc<RP> gram;
-    if (!NORM) gram.init();
+    gram.init();
     float cs[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};  // Kahan: per-column sums
     for (int64_t base = (int64_t)blockIdx.x * ROWS; base < rows; base += (int64_t)gridDim.x * ROWS) {
         const int nr = (int)(rows - base < ROWS ? rows - base : ROWS);
@@ -378,16 +354,11 @@ __global__ void __launch_bounds__(256, 2) apply_kernel(const float* __restrict__
             v[i][2] = lo2(acc[i][1]);
             v[i][3] = hi2(acc[i][1]);
             if (rg + i * RG < nr) {
-                if (NORM) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) part[q] = fmaf(v[i][q], v[i][q], part[q]);
-                } else {
-                    const float4 mv = *reinterpret_cast<const float4*>(m + (rg + i * RG) * LD + c0);
-                    part[0] = fmaf(mv.x, v[i][0], part[0]);
-                    part[1] = fmaf(mv.y, v[i][1], part[1]);
-                    part[2] = fmaf(mv.z, v[i][2], part[2]);
-                    part[3] = fmaf(mv.w, v[i][3], part[3]);
-                }
+                const float4 mv = *reinterpret_cast<const float4*>(m + (rg + i * RG) * LD + c0);
+                part[0] = fmaf(mv.x, v[i][0], part[0]);
+                part[1] = fmaf(mv.y, v[i][1], part[1]);
+                part[2] = fmaf(mv.z, v[i][2], part[2]);
+                part[3] = fmaf(mv.w, v[i][3], part[3]);
             }
         }
 #pragma unroll
@@ -397,7 +368,6 @@ __global__ void __launch_bounds__(256, 2) apply_kernel(const float* __restrict__
             cc[q] = (t - cs[q]) - y;
             cs[q] = t;
         }
-        if (NORM) continue;
         __syncthreads();  // every read of the M tile is done: reuse it for A
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -416,13 +386,12 @@ __global__ void __launch_bounds__(256, 2) apply_kernel(const float* __restrict__
         __syncthreads();
         gram.add(m, nr, LD);
     }
-    if (!NORM) gram.flush(red, p.ga, R);
+    gram.flush(red, p.ga, R);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         if (c0 + q < R) atomicAdd(&colr[c0 + q], (double)cs[q] - (double)cc[q]);
     __syncthreads();
-    double* dst = NORM ? p.colsq : p.ip;
-    for (int e = tid; e < R; e += blockDim.x) atomicAdd(dst + e, colr[e]);
+    for (int e = tid; e < R; e += blockDim.x) atomicAdd(p.ip + e, colr[e]);
 }
 
 // One block: when the update succeeded, grams[mode] = the new Gram; after the
@@ -449,10 +418,10 @@ __global__ void __launch_bounds__(256) finish_kernel(AlsParams p) {
     double xy = 0.0, yy = 0.0;
     for (int e = tid; e < R * R; e += blockDim.x) {
         const int a = e / R, b = e - a * R;
-        double v = p.lam64[a] * p.lam64[b];
+        double v = 1.0;
         for (int n = 0; n < p.N; ++n) v *= p.grams[(int64_t)n * R * R + e];
         yy += v;
-        if (a == b) xy += p.lam64[a] * p.ip[a];
+        if (a == b) xy += p.ip[a];
     }
     const int warp = tid >> 5, lane = tid & 31;
     for (int o = 16; o > 0; o >>= 1) {
@@ -478,6 +447,43 @@ __global__ void __launch_bounds__(256) finish_kernel(AlsParams p) {
         p.stats[2] = xx;
         p.stats[3] = xs;
         p.stats[4] = ys;
+    }
+}
+
+// A[:, r] /= ||A[:, r]|| with the norms from the diagonal of the factor's Gram
+// (columns of zeros stay zero).
+__global__ void __launch_bounds__(256) normalize_kernel(float* __restrict__ A, int64_t rows, int R,
+                                                        const double* __restrict__ G) {
+    __shared__ float inv[kAlsMaxRank];
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        const double d = G[r * R + r];
+        inv[r] = d > 0.0 ? (float)(1.0 / sqrt(d)) : 0.f;
+    }
+    __syncthreads();
+    const int64_t n = rows * R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        A[e] *= inv[e % R];
+}
+
+// lambda_r = prod_n ||A_n[:, r]||; every Gram scaled to the unit-norm factors.
+// Runs after the normalize_kernel launches (which read the old diagonals).
+__global__ void __launch_bounds__(256) lambda_kernel(double* __restrict__ grams, int N, int R,
+                                                     float* __restrict__ lambda) {
+    __shared__ double nrm[AMPED_MAX_MODES * kAlsMaxRank];
+    for (int e = threadIdx.x; e < N * R; e += blockDim.x) {
+        const double d = grams[(int64_t)(e / R) * R * R + (e % R) * (R + 1)];
+        nrm[e] = d > 0.0 ? sqrt(d) : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        double l = 1.0;
+        for (int n = 0; n < N; ++n) l *= nrm[n * R + r];
+        lambda[r] = (float)l;
+    }
+    for (int e = threadIdx.x; e < N * R * R; e += blockDim.x) {
+        const int n = e / (R * R), a = (e / R) % R, b = e % R;
+        const double d = nrm[n * R + a] * nrm[n * R + b];
+        grams[e] = d > 0.0 ? grams[e] / d : 0.0;
     }
 }
 
@@ -541,32 +547,42 @@ int launch_als_solve(const AlsParams& p, void* stream, int* launched) {
     return (int)cudaGetLastError();
 }
 
-template <int RP>
-static void apply_passes(const AlsParams& p, const float* M, int64_t rows, float* A, cudaStream_t st, int* launched) {
-    const int rows_per_block = 4 * (256 / (RP / 4));
-    apply_kernel<RP, true><<<grid_for(rows, rows_per_block, resident(apply_kernel<RP, true>)), 256, 0, st>>>(
-        M, rows, p, A);
-    apply_kernel<RP, false><<<grid_for(rows, rows_per_block, resident(apply_kernel<RP, false>)), 256, 0, st>>>(
-        M, rows, p, A);
-    *launched += 2;
-}
-
 int launch_als_apply(const AlsParams& p, const float* M, int64_t rows, float* A, void* stream, int* launched) {
     if (p.R < 1 || p.R > kAlsMaxRank) return (int)cudaErrorInvalidValue;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int R = p.R;
-    // colsq [R], ga [R][R], ip [R] are contiguous in the workspace
-    cudaError_t e = cudaMemsetAsync(p.colsq, 0, sizeof(double) * ((size_t)R * R + 2 * R), st);
+    cudaError_t e = cudaMemsetAsync(p.ga, 0, sizeof(double) * ((size_t)R * R + R), st);  // ga, then ip
     if (e != cudaSuccess) return (int)e;
     if (rows > 0) {
+#define AMPED_APPLY_CASE(RP)                                                                                    \
+    case RP:                                                                                                   \
+        apply_kernel<RP><<<grid_for(rows, 4 * (256 / (RP / 4)), resident(apply_kernel<RP>)), 256, 0, st>>>(M, rows, p, A); \
+        break;
         switch (padded_rank(R)) {
-            case 8: apply_passes<8>(p, M, rows, A, st, launched); break;
-            case 16: apply_passes<16>(p, M, rows, A, st, launched); break;
-            case 32: apply_passes<32>(p, M, rows, A, st, launched); break;
-            default: apply_passes<64>(p, M, rows, A, st, launched); break;
+            AMPED_APPLY_CASE(8)
+            AMPED_APPLY_CASE(16)
+            AMPED_APPLY_CASE(32)
+            default: AMPED_APPLY_CASE(64)
         }
+#undef AMPED_APPLY_CASE
+        ++*launched;
     }
     finish_kernel<<<1, 256, 0, st>>>(p);
+    ++*launched;
+    return (int)cudaGetLastError();
+}
+
+int launch_als_normalize(float* const* factors, const int64_t* dims, int N, int R, double* grams, float* lambda,
+                         void* stream, int* launched) {
+    if (R < 1 || R > kAlsMaxRank || N < 1 || N > AMPED_MAX_MODES) return (int)cudaErrorInvalidValue;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int n = 0; n < N; ++n) {
+        const int64_t elems = dims[n] * R;
+        normalize_kernel<<<grid_for(elems, 256 * 8, 8), 256, 0, st>>>(factors[n], dims[n], R,
+                                                                        grams + (size_t)n * R * R);
+        ++*launched;
+    }
+    lambda_kernel<<<1, 256, 0, st>>>(grams, N, R, lambda);
     ++*launched;
     return (int)cudaGetLastError();
 }

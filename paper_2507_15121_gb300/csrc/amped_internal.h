@@ -158,11 +158,8 @@ struct SampleParams {
 struct AlsParams {
     double* grams;       // [N][R][R] Grams of the current factors; row `mode` is replaced on success
     float* w;            // [R][R] V^-1, fp32 (workspace)
-    float* lambda;       // [R] column norms of the unnormalised update (caller's buffer)
-    double* lam64;       // [R] the same norms in fp64 (workspace)
-    double* colsq;       // [R] squared column norms of M V^-1, then (contiguous) ...
-    double* ga;          // [R][R] ... the Gram of the stored update, then ...
-    double* ip;          // [R] ... sum_i M(i,r) A(i,r) of the stored update
+    double* ga;          // [R][R] Gram of the stored update, then (contiguous) ...
+    double* ip;          // [R] ... sum_i M(i,r) A(i,r) of the stored update (workspace)
     int* info;           // 0, or the first failed Cholesky pivot + 1
     double* stats;       // [8] fit terms (written after the last mode), failure counters
     double xnorm2;       // ||X||^2
@@ -173,9 +170,12 @@ int als_max_rank();
 int launch_gram(const float* A, int64_t rows, int R, double* G, void* stream, int* launched);
 // Cholesky solve: w = V^-1, info.
 int launch_als_solve(const AlsParams& p, void* stream, int* launched);
-// Norm pass and apply pass (A = M W diag(1/lambda), its Gram, ip) unless the
-// solve failed, then the commit of the Gram and, after the last mode, the fit.
+// A = M W with its Gram and ip unless the solve failed, then the commit of the
+// Gram and, after the last mode, the fit.
 int launch_als_apply(const AlsParams& p, const float* M, int64_t rows, float* A, void* stream, int* launched);
+// Unit-norm columns for every factor, lambda = product of the norms, Grams rescaled.
+int launch_als_normalize(float* const* factors, const int64_t* dims, int N, int R, double* grams, float* lambda,
+                         void* stream, int* launched);
 
 // Split-row combine launcher (combine.cu).  Returns a cudaError_t value as
 // int, counts the kernels it launched, never synchronises.

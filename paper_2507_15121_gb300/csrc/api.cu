@@ -128,7 +128,7 @@ struct amped_tensor {
     size_t stage_out_bytes[AMPED_MAX_MODES] = {};
     double xnorm2 = 0.0;        // ||X||^2, repeated coordinates summed
     float* als_m = nullptr;     // CP-ALS: MTTKRP output [max dim][als_rcap]
-    double* als_gm = nullptr;   // CP-ALS: column sums [R], the update's Gram [R][R], ip [R], lambda [R]
+    double* als_gm = nullptr;   // CP-ALS: the update's Gram [R][R], then ip [R]
     float* als_w = nullptr;     // CP-ALS: solve output [R][R]
     int* als_info = nullptr;    // CP-ALS: solve status
     int als_rcap = 0;
@@ -206,8 +206,7 @@ amped_status ensure_als(amped_tensor* t, int R) {
     t->als_rcap = 0;
     cudaError_t e;
     if ((e = t->dalloc(reinterpret_cast<void**>(&t->als_m), (size_t)rows * R * sizeof(float))) != cudaSuccess ||
-        (e = t->dalloc(reinterpret_cast<void**>(&t->als_gm), ((size_t)R * R + 3 * R) * sizeof(double))) !=
-            cudaSuccess ||
+        (e = t->dalloc(reinterpret_cast<void**>(&t->als_gm), ((size_t)R * R + R) * sizeof(double))) != cudaSuccess ||
         (e = t->dalloc(reinterpret_cast<void**>(&t->als_w), (size_t)R * R * sizeof(float))) != cudaSuccess ||
         (e = t->dalloc(reinterpret_cast<void**>(&t->als_info), 16)) != cudaSuccess)
         return cuda_fail(e, "CP-ALS workspace allocation");
@@ -700,12 +699,11 @@ amped_status amped_tensor_norm2(amped_tensor_t t, double* norm2) {
     return AMPED_OK;
 }
 
-amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, float* lambda, double* grams,
-                                double* stats, int flags, void* stream) {
+amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, double* grams, double* stats,
+                                int flags, void* stream) {
     g_err.clear();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
-    if (!factors || !lambda || !grams || !stats)
-        return fail(AMPED_ERR_INVALID, "factors, lambda, grams or stats is NULL");
+    if (!factors || !grams || !stats) return fail(AMPED_ERR_INVALID, "factors, grams or stats is NULL");
     if (flags & ~AMPED_ALS_INIT) return fail(AMPED_ERR_INVALID, "unknown flags 0x%x", flags);
     if (R < 1) return fail(AMPED_ERR_INVALID, "rank R=%d must be >= 1", R);
     if (R > als_max_rank()) return fail(AMPED_ERR_UNSUPPORTED, "CP-ALS is built for ranks up to %d", als_max_rank());
@@ -717,8 +715,7 @@ amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, 
     if (s != AMPED_OK) return s;
     for (int n = 0; n < t->N; ++n)
         if (!aligned(factors[n], 16)) return fail(AMPED_ERR_INVALID, "factor %d is not 16-byte aligned", n);
-    if (!aligned(grams, 8) || !aligned(stats, 8) || !aligned(lambda, 4))
-        return fail(AMPED_ERR_INVALID, "lambda, grams or stats is misaligned");
+    if (!aligned(grams, 8) || !aligned(stats, 8)) return fail(AMPED_ERR_INVALID, "grams or stats is misaligned");
     if ((s = ensure_als(t, R)) != AMPED_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int launched = 0, rc = 0;
@@ -733,12 +730,9 @@ amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, 
         launched = 0;
         AlsParams p{};
         p.grams = grams;
-        p.colsq = t->als_gm;
-        p.ga = p.colsq + R;
+        p.ga = t->als_gm;
         p.ip = p.ga + (size_t)R * R;
-        p.lam64 = p.ip + R;
         p.w = t->als_w;
-        p.lambda = lambda;
         p.info = t->als_info;
         p.stats = stats;
         p.xnorm2 = t->xnorm2;
@@ -751,6 +745,23 @@ amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, 
         g_launches += launched;
         if (rc != 0) return cuda_fail((cudaError_t)rc, "CP-ALS kernel launch");
     }
+    return AMPED_OK;
+}
+
+amped_status amped_cp_als_normalize(amped_tensor_t t, float* const* factors, int R, double* grams, float* lambda,
+                                    void* stream) {
+    g_err.clear();
+    if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
+    if (!factors || !grams || !lambda) return fail(AMPED_ERR_INVALID, "factors, grams or lambda is NULL");
+    if (R < 1 || R > als_max_rank())
+        return fail(AMPED_ERR_UNSUPPORTED, "CP-ALS is built for ranks 1 to %d", als_max_rank());
+    for (int n = 0; n < t->N; ++n)
+        if (!factors[n] || !aligned(factors[n], 4)) return fail(AMPED_ERR_INVALID, "factor %d is NULL or misaligned", n);
+    if (!aligned(grams, 8) || !aligned(lambda, 4)) return fail(AMPED_ERR_INVALID, "grams or lambda is misaligned");
+    int launched = 0;
+    const int rc = launch_als_normalize(factors, t->dims, t->N, R, grams, lambda, stream, &launched);
+    g_launches += launched;
+    if (rc != 0) return cuda_fail((cudaError_t)rc, "CP-ALS normalisation launch");
     return AMPED_OK;
 }
 

@@ -192,36 +192,50 @@ class Tensor:
         _lib.check(_lib.lib().amped_tensor_norm2(self.handle, ctypes.byref(v)))
         return v.value
 
-    def cp_als_sweep(self, factors, lam, grams, stats, init: bool = False, stream=None) -> None:
-        """One CP-ALS sweep over modes 0..N-1 (least-squares update of each
-        factor after its MTTKRP, columns normalised into `lam`).  Updates the
-        fp32 `factors`, `lam` [R], `grams` [N, R, R] fp64 and `stats` [8] fp64
-        in place (stats: fit, residual^2, ||X||^2, <X, X^>, ||X^||^2, singular
-        solves, first singular mode + 1).  init=True computes `grams` from the
-        factors first."""
+    def _als_buffers(self, factors, grams, stats=None):
         fp, code, R = self._factors(factors)
         if code != _lib.F32:
             raise ValueError("CP-ALS keeps fp32 factors")
-        for name, t, dt, shape in (("lam", lam, torch.float32, (R,)), ("grams", grams, torch.float64,
-                                                                       (self.nmodes, R, R)),
+        for name, t, dt, shape in (("grams", grams, torch.float64, (self.nmodes, R, R)),
                                    ("stats", stats, torch.float64, (8,))):
+            if t is None:
+                continue
             if t.dtype != dt or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != shape:
                 raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor of shape {shape}")
-        _lib.check(_lib.lib().amped_cp_als_sweep(self.handle, fp, R, lam.data_ptr(), grams.data_ptr(),
-                                                 stats.data_ptr(), _lib.ALS_INIT if init else 0,
-                                                 _stream_ptr(stream)))
+        return fp, R
+
+    def cp_als_sweep(self, factors, grams, stats, init: bool = False, stream=None) -> None:
+        """One CP-ALS sweep over modes 0..N-1: each fp32 factor is replaced by
+        the least-squares update after its MTTKRP (columns not normalised).
+        Updates `grams` [N, R, R] fp64 (the factors' Grams) and `stats` [8]
+        fp64 in place (fit, residual^2, ||X||^2, <X, X^>, ||X^||^2, singular
+        solves, first singular mode + 1).  init=True computes `grams` from the
+        factors first."""
+        fp, R = self._als_buffers(factors, grams, stats)
+        _lib.check(_lib.lib().amped_cp_als_sweep(self.handle, fp, R, grams.data_ptr(), stats.data_ptr(),
+                                                 _lib.ALS_INIT if init else 0, _stream_ptr(stream)))
+
+    def cp_als_normalize(self, factors, grams, lam=None, stream=None):
+        """Scale every factor's columns to unit norm in place; returns lambda
+        (the products of the norms) and rescales `grams`."""
+        fp, R = self._als_buffers(factors, grams)
+        if lam is None:
+            lam = torch.empty(R, dtype=torch.float32, device=self.device)
+        _lib.check(_lib.lib().amped_cp_als_normalize(self.handle, fp, R, grams.data_ptr(), lam.data_ptr(),
+                                                     _stream_ptr(stream)))
+        return lam
 
     def cp_als(self, factors, sweeps: int = 25, tol: float = 1e-5, stream=None):
         """CP decomposition by alternating least squares, starting from the
-        given fp32 factors (updated in place).  Stops after `sweeps` sweeps or
-        when the fit changes by less than `tol`.  Returns (lam, fits)."""
+        given fp32 factors (updated in place, unit-norm columns on return).
+        Stops after `sweeps` sweeps or when the fit changes by less than
+        `tol`.  Returns (lambda, fits)."""
         R = int(factors[0].shape[1])
-        lam = torch.empty(R, dtype=torch.float32, device=self.device)
         grams = torch.empty((self.nmodes, R, R), dtype=torch.float64, device=self.device)
         stats = torch.zeros(8, dtype=torch.float64, device=self.device)
         fits = []
         for s in range(sweeps):
-            self.cp_als_sweep(factors, lam, grams, stats, init=(s == 0), stream=stream)
+            self.cp_als_sweep(factors, grams, stats, init=(s == 0), stream=stream)
             if stream is not None:
                 stream.synchronize()
             st = stats.cpu()
@@ -231,7 +245,7 @@ class Tensor:
             fits.append(float(st[0]))
             if s > 0 and abs(fits[-1] - fits[-2]) < tol:
                 break
-        return lam, fits
+        return self.cp_als_normalize(factors, grams, stream=stream), fits
 
     def set_kernel_events(self, start, stop) -> None:
         """Record torch.cuda.Event `start`/`stop` around the next MTTKRP kernel."""

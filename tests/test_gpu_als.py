@@ -46,20 +46,31 @@ def col_error(gpu, ref):
 
 
 def gpu_sweeps(dims, idx, vals, F, sweeps=1):
+    """(factors as stored after the sweeps, their Grams, stats after every sweep,
+    ||X||^2, (unit-norm factors, lambda, Grams) from amped_cp_als_normalize)."""
     t = amped.Tensor(dims, idx, vals)
     Fd = to_dev(F)
     R = F[0].shape[1]
-    lam = torch.empty(R, device="cuda")
     grams = torch.empty((len(dims), R, R), dtype=torch.float64, device="cuda")
     stats = torch.zeros(8, dtype=torch.float64, device="cuda")
     hist = []
     for s in range(sweeps):
-        t.cp_als_sweep(Fd, lam, grams, stats, init=(s == 0))
+        t.cp_als_sweep(Fd, grams, stats, init=(s == 0))
         torch.cuda.synchronize()
         hist.append(stats.cpu().numpy().copy())
-    out = [f.cpu().numpy() for f in Fd], lam.cpu().numpy().astype(np.float64), grams.cpu().numpy(), hist, t.norm2()
+    A, G = [f.cpu().numpy() for f in Fd], grams.cpu().numpy()
+    lam = t.cp_als_normalize(Fd, grams)
+    torch.cuda.synchronize()
+    normed = [f.cpu().numpy() for f in Fd], lam.cpu().numpy().astype(np.float64), grams.cpu().numpy()
+    n2 = t.norm2()
     t.close()
-    return out
+    return A, G, hist, n2, normed
+
+
+def unit(A):
+    A = np.asarray(A, dtype=np.float64)
+    n = np.linalg.norm(A, axis=0)
+    return A / np.where(n > 0, n, 1.0)
 
 
 def check_fit_terms(dims, idx, vals, A, lam, st):
@@ -89,7 +100,7 @@ CASES = [("uniform3", None, 16), ("zipf3", 0.0005, 32), ("zipf4", 0.0001, 32), (
 def test_one_sweep_matches_oracle(name, scale, R):
     w, c = workload(name, scale)
     F = synth.factors(c.dims, R, w.seed)
-    Ag, lam_g, grams_g, hist, n2 = gpu_sweeps(c.dims, c.idx, c.vals, F)
+    Ag, Gg, hist, n2, (An, lam_n, Gn) = gpu_sweeps(c.dims, c.idx, c.vals, F)
     N = c.nmodes
     for n in range(N):
         # the inputs mode n saw: updated factors before it, starting factors after it
@@ -97,29 +108,37 @@ def test_one_sweep_matches_oracle(name, scale, R):
         V = als.hadamard_others([als.gram(a) for a in inp], n)
         bar = 4 * np.linalg.cond(V) * (EPS_M + R * 2.0 ** -24)
         A_o, lam_o = als.update_mode(c.dims, c.idx, c.vals, inp, n)
-        err = col_error(Ag[n], A_o)
+        err = col_error(unit(Ag[n]), A_o)  # directions; the GPU keeps the update unnormalised
         assert err <= bar, (n, err, bar)
-        np.testing.assert_allclose(np.linalg.norm(Ag[n].astype(np.float64), axis=0), 1.0, atol=max(1e-5, bar))
+        assert np.abs(np.linalg.norm(Ag[n].astype(np.float64), axis=0) / lam_o - 1).max() <= bar, n
         G = als.gram(Ag[n])  # the Gram of what was stored
-        assert np.abs(grams_g[n] - G).max() <= 1e-6 * np.abs(G).max(), n
-        if n == N - 1:
-            assert np.abs(lam_g - lam_o).max() <= bar * np.abs(lam_o).max()
+        assert np.abs(Gg[n] - G).max() <= 1e-6 * np.abs(G).max(), n
     st = hist[0]
-    check_fit_terms(c.dims, c.idx, c.vals, Ag, lam_g, st)
+    check_fit_terms(c.dims, c.idx, c.vals, Ag, np.ones(R), st)
     assert st[5] == 0 and st[6] == 0
     assert abs(n2 - als.norm2(c.idx, c.vals)) <= 1e-12 * n2
     assert st[2] == n2
+    # amped_cp_als_normalize: the same model with unit-norm columns
+    norms = [np.linalg.norm(a.astype(np.float64), axis=0) for a in Ag]
+    np.testing.assert_allclose(lam_n, np.prod(norms, axis=0), rtol=1e-5)
+    for n in range(N):
+        np.testing.assert_allclose(np.linalg.norm(An[n].astype(np.float64), axis=0), 1.0, atol=1e-5)
+        np.testing.assert_allclose(An[n], unit(Ag[n]), rtol=1e-5, atol=1e-7)
+        G = als.gram(An[n])
+        assert np.abs(Gn[n] - G).max() <= 1e-5 * np.abs(G).max(), n
+    xx, xy, yy = als.fit_terms(c.dims, c.idx, c.vals, [a.astype(np.float64) for a in An], lam_n)
+    assert abs(xy - st[3]) <= TERM_BAR * (xx + yy) and abs(yy - st[4]) <= TERM_BAR * (xx + yy)
 
 
 def test_sweeps_track_the_oracle_fit():
     w, c = workload("zipf3", 0.0005)
     F = synth.factors(c.dims, 16, w.seed)
-    Ag, lam_g, _, hist, _ = gpu_sweeps(c.dims, c.idx, c.vals, F, sweeps=6)
+    Ag, _, hist, _, _ = gpu_sweeps(c.dims, c.idx, c.vals, F, sweeps=6)
     _, _, fits_o = als.run(c.dims, c.idx, c.vals, F, 6)
     got = np.array([s[0] for s in hist])
     assert np.all(np.abs(got - np.array(fits_o)) <= 1e-3), (got, fits_o)
     assert np.all(np.diff(got) >= -1e-5)  # ALS does not increase the residual
-    check_fit_terms(c.dims, c.idx, c.vals, Ag, lam_g, hist[-1])
+    check_fit_terms(c.dims, c.idx, c.vals, Ag, np.ones(16), hist[-1])
 
 
 def block_low_rank(R, block, seed):
@@ -142,14 +161,18 @@ def test_exact_low_rank_sparse_tensor_is_recovered():
     dims, idx, vals, B = block_low_rank(6, (20, 15, 10), 3)
     rng = np.random.default_rng(4)
     F = [(b + 0.05 * rng.uniform(0, 1, b.shape)).astype(np.float32) for b in B]  # start near the truth
-    Ag, lam_g, _, hist, _ = gpu_sweeps(dims, idx, vals, F, sweeps=30)
+    Ag, _, hist, _, (An, lam_n, _) = gpu_sweeps(dims, idx, vals, F, sweeps=30)
     # the fit of the stored model, evaluated by the oracle in fp64: fp32 factors reach ~1e-7
-    true_fit = als.fit(dims, idx, vals, [a.astype(np.float64) for a in Ag], lam_g)
+    true_fit = als.fit(dims, idx, vals, [a.astype(np.float64) for a in An], lam_n)
     assert true_fit > 1 - 1e-5, true_fit
     # the library's own fit is the fp64 expansion of fp32-accurate terms: near a perfect fit its
     # resolution is sqrt(TERM_BAR * (||X||^2 + ||X^||^2)) / ||X||
     assert hist[-1][0] > 1 - np.sqrt(2 * TERM_BAR), hist[-1][0]
-    check_fit_terms(dims, idx, vals, Ag, lam_g, hist[-1])
+    check_fit_terms(dims, idx, vals, Ag, np.ones(6), hist[-1])
+    # each planted block is recovered by one component (up to the order of the components)
+    for n in range(3):
+        cos = np.abs(unit(B[n]).T @ An[n].astype(np.float64))
+        assert np.all(cos.max(axis=1) > 1 - 1e-5), cos.max(axis=1)
 
 
 def test_singular_normal_equations_are_reported():
@@ -161,10 +184,9 @@ def test_singular_normal_equations_are_reported():
     t = amped.Tensor(c.dims, c.idx, c.vals)
     Fd = to_dev(F)
     before = Fd[0].clone()
-    lam = torch.empty(R, device="cuda")
     grams = torch.empty((3, R, R), dtype=torch.float64, device="cuda")
     stats = torch.zeros(8, dtype=torch.float64, device="cuda")
-    t.cp_als_sweep(Fd, lam, grams, stats, init=True)
+    t.cp_als_sweep(Fd, grams, stats, init=True)
     torch.cuda.synchronize()
     st = stats.cpu().numpy()
     assert st[5] >= 1 and st[6] == 1  # mode 0 failed first
@@ -178,15 +200,16 @@ def test_argument_errors():
     w, c = workload("zipf3", 0.0002)
     t = amped.Tensor(c.dims, c.idx, c.vals)
     F = to_dev(synth.factors(c.dims, 72, w.seed))
-    lam = torch.empty(72, device="cuda")
     grams = torch.empty((3, 72, 72), dtype=torch.float64, device="cuda")
     stats = torch.zeros(8, dtype=torch.float64, device="cuda")
     with pytest.raises(amped.AmpedError) as e:
-        t.cp_als_sweep(F, lam, grams, stats, init=True)
+        t.cp_als_sweep(F, grams, stats, init=True)
     assert e.value.status == amped._lib.ERR_UNSUPPORTED
+    with pytest.raises(amped.AmpedError):
+        t.cp_als_normalize(F, grams)
     Fb = [f[:, :32].contiguous().to(torch.bfloat16) for f in F]
     with pytest.raises(ValueError):
-        t.cp_als_sweep(Fb, lam[:32].contiguous(), grams[:, :32, :32].contiguous(), stats, init=True)
+        t.cp_als_sweep(Fb, grams[:, :32, :32].contiguous(), stats, init=True)
     with pytest.raises(ValueError):  # wrong Gram shape
-        t.cp_als_sweep([f[:, :32].contiguous() for f in F], lam[:32].contiguous(), grams, stats)
+        t.cp_als_sweep([f[:, :32].contiguous() for f in F], grams, stats)
     t.close()
