@@ -285,111 +285,232 @@ __global__ void __launch_bounds__(256) solve_kernel(AlsParams p) {
     if (tid == 0) *p.info = 0;
 }
 
+// Asynchronous global -> shared copies (no registers in flight), in groups.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shape of apply_kernel for padded rank RP: CT column groups of 4, RG row
+// groups, 4 rows per thread (rows rg, rg + RG, rg + 2 RG, rg + 3 RG of a tile,
+// so the rows a warp reads together are consecutive and hit different banks).
+template <int RP>
+struct ApplyShape {
+    static constexpr int CT = RP / 4;
+    static constexpr int RG = 256 / CT;
+    static constexpr int ROWS = 4 * RG;  // rows per tile
+    static constexpr int LD = RP + 4;    // M tile row stride (floats)
+    // two M tiles, the transposed A tile [RP][ROWS], W^T [RP][RP]
+    static constexpr size_t smem_bytes() {
+        return sizeof(float) * ((size_t)2 * ROWS * LD + (size_t)RP * ROWS + (size_t)RP * RP);
+    }
+};
+
+// Row-major [n][RP] arrays whose row c has its 4-float chunks XOR-swizzled by
+// the column group c / 4: the eight column groups of a warp that read the same
+// k (or the same rows) land in eight different bank groups.
+__device__ __forceinline__ int swz(int c, int k, int stride) { return c * stride + (k ^ (((c >> 2) & 7) << 2)); }
+
+// Copies rows [base, base + nr) of M into a tile (row stride LD) without
+// registers; columns >= R and rows >= nr are left as they are.
+__device__ __forceinline__ void stage_async(const float* __restrict__ M, int64_t base, int nr, int R, float* tile,
+                                            int LD) {
+    const float* src = M + base * R;
+    if ((R & 3) == 0) {
+        const int q = R / 4, n = nr * q;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int row = e / q, c = (e - row * q) * 4;
+            cp_async16(tile + row * LD + c, src + (int64_t)row * R + c);
+        }
+    } else {
+        const int n = nr * R;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int row = e / R;
+            cp_async4(tile + row * LD + e - row * R, src + e);
+        }
+    }
+    cp_async_commit();
+}
+
 // A = M W for the MTTKRP output M (row-major [rows][R]) and the solve's
 // W = V^-1 (fp32), stored; in the same pass ga += A^T A (of the fp32 values
 // stored) and ip[r] += sum_i M(i,r) A(i,r).  Does nothing when the solve
-// reported a singular V.  RP = R rounded up to 8, 16, 32 or 64; a thread
-// computes 4 rows x 4 columns: rows rg, rg + RG, rg + 2 RG, rg + 3 RG of the
-// staged block (consecutive row groups hit different shared-memory banks).
+// reported a singular V.  RP = R rounded up to 8, 16, 32 or 64.  Tiles of M
+// are double-buffered with cp.async.  The product uses packed f32x2 FMA with
+// the operand pairs loaded as 64-bit words: (M[i][k], M[i][k+1]) x
+// (W[k][c], W[k+1][c]), W^T in shared memory.  The Gram reads A^T from shared
+// memory, four rows of two columns per pair of 128-bit loads.
 template <int RP>
 __global__ void __launch_bounds__(256, 2) apply_kernel(const float* __restrict__ M, int64_t rows, AlsParams p,
                                                        float* __restrict__ A) {
-    constexpr int CT = RP / 4;    // column tiles
-    constexpr int RG = 256 / CT;  // row groups
-    constexpr int ROWS = 4 * RG;  // rows per block iteration
-    constexpr int LD = RP + 4;
-    // W, then the M tile (reused for the A tile); the Gram's block reduction
-    // reuses the same storage once the loop is done
-    constexpr int kFloats = (RP + ROWS) * LD;
-    static_assert(GramAcc<RP>::TILES * 16 * 2 <= kFloats, "reduction does not fit");
-    __shared__ __align__(16) float sm[kFloats];
+    using SH = ApplyShape<RP>;
+    constexpr int CT = SH::CT, RG = SH::RG, ROWS = SH::ROWS, LD = SH::LD;
+    constexpr int NT = RP / 4, TILES = NT * (NT + 1) / 2, GROUPS = 256 / TILES;
+    static_assert(GROUPS >= 1 && TILES * 16 * 2 <= 2 * ROWS * LD, "Gram reduction must fit in the M tiles");
+    extern __shared__ __align__(16) float dsm[];
+    float* buf0 = dsm;
+    float* buf1 = dsm + ROWS * LD;
+    float* at = dsm + 2 * ROWS * LD;  // A^T [RP][ROWS], swizzled
+    float* wt = at + RP * ROWS;       // W^T [RP][RP], swizzled
     __shared__ double colr[RP];
-    float* w = sm;
-    float* m = sm + RP * LD;
-    double* red = reinterpret_cast<double*>(sm);
     if (*p.info) return;
     const int R = p.R;
     const int tid = threadIdx.x, ct = tid % CT, rg = tid / CT, c0 = ct * 4;
-    for (int e = tid; e < RP * LD; e += blockDim.x) {
-        const int k = e / LD, col = e - k * LD;
-        w[e] = (k < R && col < R) ? p.w[k * R + col] : 0.f;
+    const int64_t step = (int64_t)gridDim.x * ROWS;
+    int64_t base = (int64_t)blockIdx.x * ROWS;
+    // zero the tiles (padding columns and rows must stay finite zeros), then W^T
+    for (int e = tid; e < 2 * ROWS * LD + RP * ROWS; e += blockDim.x) dsm[e] = 0.f;
+    for (int e = tid; e < RP * RP; e += blockDim.x) {
+        const int c = e / RP, k = e - c * RP;
+        wt[swz(c, k, RP)] = (k < R && c < R) ? p.w[k * R + c] : 0.f;
     }
-    for (int e = tid; e < ROWS * LD; e += blockDim.x) m[e] = 0.f;  // padding columns stay zero
-    for (int e = tid; e < RP; e += blockDim.x) colr[e] = 0.0;   // per-column block sums of ip
-    GramAcc<RP> gram;
-    gram.init();
-    float cs[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};  // Kahan: per-column sums
-    for (int64_t base = (int64_t)blockIdx.x * ROWS; base < rows; base += (int64_t)gridDim.x * ROWS) {
+    for (int e = tid; e < RP; e += blockDim.x) colr[e] = 0.0;
+    __syncthreads();
+    if (base < rows) stage_async(M, base, (int)(rows - base < ROWS ? rows - base : ROWS), R, buf0, LD);
+    // Gram share of this thread: the 4x4 tile (ta, tb), ta <= tb, of group g
+    const int g = tid / TILES, kt = tid - g * TILES;
+    int ta = 0, tb = 0;
+    tri_tile(kt, NT, ta, tb);
+    float gs[16], gc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) gs[j] = gc[j] = 0.f;
+    float is[4] = {0.f, 0.f, 0.f, 0.f}, ic[4] = {0.f, 0.f, 0.f, 0.f};
+    int cur = 0;
+    for (; base < rows; base += step, cur ^= 1) {
         const int nr = (int)(rows - base < ROWS ? rows - base : ROWS);
-        __syncthreads();
-        stage_rows(M, base, nr, R, m, LD);
-        __syncthreads();
-        unsigned long long acc[4][2];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0ull;
-#pragma unroll 2
-        for (int k = 0; k < RP; k += 4) {
-            float4 a[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(m + (rg + i * RG) * LD + k);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float4 b = *reinterpret_cast<const float4*>(w + (k + j) * LD + c0);
-                const unsigned long long b01 = pack2(b.x, b.y), b23 = pack2(b.z, b.w);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float av = j == 0 ? a[i].x : j == 1 ? a[i].y : j == 2 ? a[i].z : a[i].w;
-                    const unsigned long long aa = pack2(av, av);
-                    acc[i][0] = ffma2(aa, b01, acc[i][0]);
-                    acc[i][1] = ffma2(aa, b23, acc[i][1]);
-                }
-            }
+        const float* tile = cur ? buf1 : buf0;
+        __syncthreads();  // the other buffer's and the A^T tile's last readers are done
+        if (base + step < rows) {
+            const int64_t nb = base + step;
+            stage_async(M, nb, (int)(rows - nb < ROWS ? rows - nb : ROWS), R, cur ? buf0 : buf1, LD);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
-        float v[4][4];
+        __syncthreads();
+        // ---- product: acc[i][q] = (sum over even k, sum over odd k) of M[row_i][k] W[k][c0+q]
+        unsigned long long acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][q] = 0ull;
+#pragma unroll 1
+        for (int k = 0; k < RP; k += 4) {
+            ulonglong2 mv[4], wv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mv[i] = *reinterpret_cast<const ulonglong2*>(tile + (rg + i * RG) * LD + k);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) wv[q] = *reinterpret_cast<const ulonglong2*>(wt + swz(c0 + q, k, RP));
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][q] = ffma2(mv[i].x, wv[q].x, acc[i][q]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][q] = ffma2(mv[i].y, wv[q].y, acc[i][q]);
+        }
+        float av[4][4];
         float part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            v[i][0] = lo2(acc[i][0]);
-            v[i][1] = hi2(acc[i][0]);
-            v[i][2] = lo2(acc[i][1]);
-            v[i][3] = hi2(acc[i][1]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) av[i][q] = lo2(acc[i][q]) + hi2(acc[i][q]);
             if (rg + i * RG < nr) {
-                const float4 mv = *reinterpret_cast<const float4*>(m + (rg + i * RG) * LD + c0);
-                part[0] = fmaf(mv.x, v[i][0], part[0]);
-                part[1] = fmaf(mv.y, v[i][1], part[1]);
-                part[2] = fmaf(mv.z, v[i][2], part[2]);
-                part[3] = fmaf(mv.w, v[i][3], part[3]);
+                const float4 m = *reinterpret_cast<const float4*>(tile + (rg + i * RG) * LD + c0);
+                part[0] = fmaf(m.x, av[i][0], part[0]);
+                part[1] = fmaf(m.y, av[i][1], part[1]);
+                part[2] = fmaf(m.z, av[i][2], part[2]);
+                part[3] = fmaf(m.w, av[i][3], part[3]);
             }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float y = part[q] - cc[q];
-            const float t = cs[q] + y;
-            cc[q] = (t - cs[q]) - y;
-            cs[q] = t;
+        for (int q = 0; q < 4; ++q) {  // Kahan across tiles
+            const float y = part[q] - ic[q];
+            const float t = is[q] + y;
+            ic[q] = (t - is[q]) - y;
+            is[q] = t;
         }
-        __syncthreads();  // every read of the M tile is done: reuse it for A
+        // ---- store A (global, row-major) and A^T (shared, for the Gram); rows >= nr are zeros in A^T
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int row = rg + i * RG;
-            if (row >= nr) continue;
-            *reinterpret_cast<float4*>(m + row * LD + c0) = make_float4(v[i][0], v[i][1], v[i][2], v[i][3]);
+            const bool ok = row < nr;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) at[swz(c0 + q, row, ROWS)] = ok ? av[i][q] : 0.f;
+            if (!ok) continue;
             float* dst = A + (base + row) * R;
             if ((R & 3) == 0) {
-                if (c0 < R) *reinterpret_cast<float4*>(dst + c0) = make_float4(v[i][0], v[i][1], v[i][2], v[i][3]);
+                if (c0 < R) *reinterpret_cast<float4*>(dst + c0) = make_float4(av[i][0], av[i][1], av[i][2], av[i][3]);
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (c0 + q < R) dst[c0 + q] = v[i][q];
+                    if (c0 + q < R) dst[c0 + q] = av[i][q];
             }
         }
         __syncthreads();
-        gram.add(m, nr, LD);
+        // ---- Gram over the tile's 4-row chunks: G[a][b] += sum_r A[r][a] A[r][b]
+        if (g < GROUPS) {
+            float ga[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) ga[j] = 0.f;
+            const int nq = (nr + 3) / 4;
+            for (int qd = g; qd < nq; qd += GROUPS) {
+                float4 a[4], b[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) a[x] = *reinterpret_cast<const float4*>(at + swz(ta * 4 + x, qd * 4, ROWS));
+#pragma unroll
+                for (int y = 0; y < 4; ++y) b[y] = *reinterpret_cast<const float4*>(at + swz(tb * 4 + y, qd * 4, ROWS));
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        float v = ga[x * 4 + y];
+                        v = fmaf(a[x].x, b[y].x, v);
+                        v = fmaf(a[x].y, b[y].y, v);
+                        v = fmaf(a[x].z, b[y].z, v);
+                        v = fmaf(a[x].w, b[y].w, v);
+                        ga[x * 4 + y] = v;
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float yv = ga[j] - gc[j];
+                const float t = gs[j] + yv;
+                gc[j] = (t - gs[j]) - yv;
+                gs[j] = t;
+            }
+        }
     }
-    gram.flush(red, p.ga, R);
+    // block reduction of the Gram (groups in a fixed order), reusing the M tiles
+    double* red = reinterpret_cast<double*>(dsm);
+    __syncthreads();
+    for (int gg = 0; gg < GROUPS; ++gg) {
+        if (g == gg)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) red[kt * 16 + j] = (gg ? red[kt * 16 + j] : 0.0) + ((double)gs[j] - (double)gc[j]);
+        __syncthreads();
+    }
+    for (int e = tid; e < TILES * 16; e += blockDim.x) {
+        int ua, ub;
+        tri_tile(e / 16, NT, ua, ub);
+        const int a = ua * 4 + (e & 15) / 4, b = ub * 4 + (e & 3);
+        if (a < R && b < R) {
+            const double v = red[e];
+            atomicAdd(p.ga + a * R + b, v);
+            if (ua != ub) atomicAdd(p.ga + b * R + a, v);
+        }
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        if (c0 + q < R) atomicAdd(&colr[c0 + q], (double)cs[q] - (double)cc[q]);
+        if (c0 + q < R) atomicAdd(&colr[c0 + q], (double)is[q] - (double)ic[q]);
     __syncthreads();
     for (int e = tid; e < R; e += blockDim.x) atomicAdd(p.ip + e, colr[e]);
 }
@@ -502,11 +623,11 @@ int grid_for(int64_t units, int per_block, int blocks_per_sm) {
     return (int)(g < 1 ? 1 : g);
 }
 
-// Blocks of `kernel` (256 threads, static shared memory) resident on one SM.
+// Blocks of `kernel` (256 threads, `dyn` bytes of dynamic shared memory) resident on one SM.
 template <class K>
-int resident(K kernel) {
+int resident(K kernel, size_t dyn = 0) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 256, 0) != cudaSuccess || n < 1) n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 256, dyn) != cudaSuccess || n < 1) n = 1;
     return n;
 }
 
@@ -555,9 +676,14 @@ int launch_als_apply(const AlsParams& p, const float* M, int64_t rows, float* A,
     if (e != cudaSuccess) return (int)e;
     if (rows > 0) {
 #define AMPED_APPLY_CASE(RP)                                                                                    \
-    case RP:                                                                                                   \
-        apply_kernel<RP><<<grid_for(rows, 4 * (256 / (RP / 4)), resident(apply_kernel<RP>)), 256, 0, st>>>(M, rows, p, A); \
-        break;
+    case RP: {                                                                                                 \
+        const size_t bytes = ApplyShape<RP>::smem_bytes();                                                     \
+        e = cudaFuncSetAttribute(apply_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);   \
+        if (e != cudaSuccess) return (int)e;                                                                   \
+        apply_kernel<RP><<<grid_for(rows, ApplyShape<RP>::ROWS, resident(apply_kernel<RP>, bytes)), 256, bytes, st>>>( \
+            M, rows, p, A);                                                                                    \
+        break;                                                                                                 \
+    }
         switch (padded_rank(R)) {
             AMPED_APPLY_CASE(8)
             AMPED_APPLY_CASE(16)
