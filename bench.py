@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the 16-bit factor variants")
     ap.add_argument("--als-sweeps", type=int, default=5, help="timed CP-ALS sweeps (0 = skip)")
+    ap.add_argument("--stream-memory", default="device", choices=["device", "host"],
+                    help="where the per-nonzero streams live (host = read over the host link, out-of-core)")
     ap.add_argument("--lowp", default="", help="16-bit factor variants to time, e.g. bf16,f16 "
                                               "(default: bf16; bf16,f16 for zipf3_r64)")
     return ap.parse_args()
@@ -163,10 +165,16 @@ def bytes_model(c, R, sf, U):
     return out
 
 
+MTTKRP_SOURCES = ("kernels.cuh", "dispatch.cuh", "mttkrp_f32.cu", "mttkrp_bf16.cu", "mttkrp_f16.cu", "combine.cu",
+                  "reorder.cpp")
+
+
 def kernel_source_hash():
+    """Hash of the sources that decide the MTTKRP kernel's memory traffic
+    (the kernel, its launch shapes, the split-row combine and the host plan)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2507_15121_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in MTTKRP_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -203,6 +211,7 @@ def workload_config(w, args):
             "factors": "fp32 U(0,1); bf16 variant rounded from the same draws",
             "segment_items": args.segment_items or "default", "inner_order": args.inner_order,
             "short_rows": args.short_rows or 32,
+            "stream_memory": getattr(args, "stream_memory", "device"),
             "l2": "inputs_exceed_l2 (no flush)",
             "parallelism": "single GPU per rank; ranks run independent replicas"}
 
@@ -308,7 +317,7 @@ def run_ours(args, w, world, rank, local, pg):
     gen_s = time.time() - t0
     t0 = time.time()
     t = amped.Tensor(c.dims, c.idx, c.vals, segment_items=args.segment_items, inner_order=args.inner_order,
-                     short_rows=args.short_rows)
+                     short_rows=args.short_rows, stream_memory=args.stream_memory)
     create_s = time.time() - t0
     stream = torch.cuda.current_stream()
     Fd = [torch.from_numpy(f).to(device) for f in F]

@@ -68,6 +68,12 @@ typedef struct {
                               sorted by length and processed one row per lane group; longer rows are
                               processed by whole warps along the merge path.  0 = default (32);
                               negative = every row with a nonzero is long */
+    int32_t stream_memory; /* where the per-nonzero streams of the copies live (coordinates, values,
+                              permutations, caller-order coordinates): 1 = device memory; 2 = pinned
+                              host memory mapped into the device's address space, read by the
+                              kernels over the host link (out-of-core: the tensor may exceed HBM;
+                              factors, outputs, row tables and scratch stay on the device);
+                              0 = default (1) */
 } amped_opts;
 
 typedef struct amped_tensor* amped_tensor_t;

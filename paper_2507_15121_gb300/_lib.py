@@ -30,7 +30,7 @@ class AmpedError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("segment_items", ctypes.c_int32), ("keep_perm", ctypes.c_int32), ("keep_coo", ctypes.c_int32),
                 ("max_rank", ctypes.c_int32), ("host_threads", ctypes.c_int32), ("inner_order", ctypes.c_int32),
-                ("short_rows", ctypes.c_int32)]
+                ("short_rows", ctypes.c_int32), ("stream_memory", ctypes.c_int32)]
 
 
 class PlanSizes(ctypes.Structure):

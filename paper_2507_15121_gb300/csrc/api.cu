@@ -132,7 +132,9 @@ struct amped_tensor {
     float* als_w = nullptr;     // CP-ALS: solve output [R][R]
     int* als_info = nullptr;    // CP-ALS: solve status
     int als_rcap = 0;
+    bool host_streams = false;      // per-nonzero streams in mapped pinned host memory
     std::vector<void*> allocs;
+    std::vector<void*> host_allocs;
 
     cudaError_t dalloc(void** p, size_t bytes) {
         *p = nullptr;
@@ -149,8 +151,20 @@ struct amped_tensor {
         if (it != allocs.end()) allocs.erase(it);
         cudaFree(p);
     }
+    // A per-nonzero stream: device memory, or mapped pinned host memory read over the host link.
+    cudaError_t salloc(void** p, size_t bytes) {
+        if (!host_streams) return dalloc(p, bytes);
+        *p = nullptr;
+        void* h = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, bytes ? bytes : 16, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) return e;
+        host_allocs.push_back(h);
+        std::memset(h, 0, bytes ? bytes : 16);  // slack included; also touches every page once
+        return cudaHostGetDevicePointer(p, h, 0);
+    }
     ~amped_tensor() {
         for (void* p : allocs) cudaFree(p);
+        for (void* p : host_allocs) cudaFreeHost(p);
     }
 };
 
@@ -162,6 +176,18 @@ cudaError_t upload(amped_tensor* t, T** dst, const T* src, size_t n, size_t cap)
     if (e != cudaSuccess) return e;
     if (cap > n) e = cudaMemset(*dst + n, 0, (cap - n) * sizeof(T));
     if (e == cudaSuccess && n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// upload() for a per-nonzero stream (device or mapped host memory; cudaMemcpyDefault
+// resolves either through unified addressing).
+template <class T>
+cudaError_t upload_stream(amped_tensor* t, T** dst, const T* src, size_t n, size_t cap) {
+    cudaError_t e = t->salloc(reinterpret_cast<void**>(dst), cap * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyDefault);
+    if (e == cudaSuccess && cap > n && !t->host_streams)  // host streams start zeroed
+        e = cudaMemset(*dst + n, 0, (cap - n) * sizeof(T));
     return e;
 }
 
@@ -352,7 +378,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
             return fail(AMPED_ERR_INVALID, "dims[%d]=%lld outside 1..2^31-%d", n, (long long)dims[n], 4 * kPad);
     if (nnz > 0 && (!idx || !vals)) return fail(AMPED_ERR_INVALID, "idx or vals is NULL");
     int items = 0, threads = 0, max_rank = 64, short_thr = 32;
-    bool keep_perm = true, keep_coo = true, inner_sort = true;
+    bool keep_perm = true, keep_coo = true, inner_sort = true, host_streams = false;
     if (opts) {
         if (opts->segment_items < 0 || opts->max_rank < 0 || opts->host_threads < 0)
             return fail(AMPED_ERR_INVALID, "negative option");
@@ -364,6 +390,9 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         inner_sort = opts->inner_order != 1;
         if (opts->short_rows > 0) short_thr = std::min(opts->short_rows, kShortNnz + 1);
         if (opts->short_rows < 0) short_thr = 1;  // every non-empty row takes the long path
+        if (opts->stream_memory < 0 || opts->stream_memory > 2)
+            return fail(AMPED_ERR_INVALID, "stream_memory=%d is not 0, 1 or 2", opts->stream_memory);
+        host_streams = opts->stream_memory == 2;
     }
     const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, threads);
     if (bad >= 0) {
@@ -378,6 +407,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
     if (items == 0) items = default_segment_items(nnz, nmodes, dims, t->device);
     t->N = nmodes;
     t->nnz = nnz;
+    t->host_streams = host_streams;
     for (int n = 0; n < nmodes; ++n) t->dims[n] = dims[n];
     t->stride = ((nnz + kPad) + 63) / 64 * 64;
     const size_t stride = (size_t)t->stride;
@@ -415,23 +445,23 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
             (e = upload(t, &dm.seg_short, hm.seg_short.p, (size_t)hm.S_S + 1, (size_t)hm.S_S + 1)) != cudaSuccess)
             return bail(cuda_fail(e, "device copy of the row tables"));
         if (nmodes > 1) {
-            if ((e = t->dalloc(reinterpret_cast<void**>(&dm.idx), (size_t)(nmodes - 1) * stride * 4)) != cudaSuccess)
-                return bail(cuda_fail(e, "device copy of the coordinates"));
+            if ((e = t->salloc(reinterpret_cast<void**>(&dm.idx), (size_t)(nmodes - 1) * stride * 4)) != cudaSuccess)
+                return bail(cuda_fail(e, "copy of the coordinates"));
             const int nin = input_slots(nmodes, dims, mode, inner_sort, dm.slot_mode);
             for (int slot = 0; slot < nin; ++slot) {
                 gather_column(hm, nmodes, idx, dm.slot_mode[slot], col.p, threads);
                 std::memset(col.p + nnz, 0, (stride - (size_t)nnz) * 4);
-                if ((e = cudaMemcpy(dm.idx + (size_t)slot * stride, col.p, stride * 4, cudaMemcpyHostToDevice)) !=
+                if ((e = cudaMemcpy(dm.idx + (size_t)slot * stride, col.p, stride * 4, cudaMemcpyDefault)) !=
                     cudaSuccess)
-                    return bail(cuda_fail(e, "device copy of the coordinates"));
+                    return bail(cuda_fail(e, "copy of the coordinates"));
             }
         }
         gather_values(hm, vals, fcol.p, threads);
         std::memset(fcol.p + nnz, 0, (stride - (size_t)nnz) * 4);
-        if ((e = upload(t, &dm.val, fcol.p, stride, stride)) != cudaSuccess)
-            return bail(cuda_fail(e, "device copy of the values"));
-        if (keep_perm && (e = upload(t, &dm.perm, hm.perm.p, (size_t)nnz, stride)) != cudaSuccess)
-            return bail(cuda_fail(e, "device copy of the permutation"));
+        if ((e = upload_stream(t, &dm.val, fcol.p, stride, stride)) != cudaSuccess)
+            return bail(cuda_fail(e, "copy of the values"));
+        if (keep_perm && (e = upload_stream(t, &dm.perm, hm.perm.p, (size_t)nnz, stride)) != cudaSuccess)
+            return bail(cuda_fail(e, "copy of the permutation"));
         std::vector<int32_t> seg((size_t)2 * (hm.S + 1));
         std::memcpy(seg.data(), hm.seg_row.p, (size_t)(hm.S + 1) * 4);
         std::memcpy(seg.data() + hm.S + 1, hm.seg_nz.p, (size_t)(hm.S + 1) * 4);
@@ -449,14 +479,13 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         t->maxTask = std::max(t->maxTask, hm.ntask);
     }
     if (keep_coo) {
-        if ((e = t->dalloc(reinterpret_cast<void**>(&t->coo), (size_t)nmodes * stride * 4)) != cudaSuccess)
-            return bail(cuda_fail(e, "device copy of the caller-order coordinates"));
+        if ((e = t->salloc(reinterpret_cast<void**>(&t->coo), (size_t)nmodes * stride * 4)) != cudaSuccess)
+            return bail(cuda_fail(e, "copy of the caller-order coordinates"));
         for (int n = 0; n < nmodes; ++n) {
             caller_column(nnz, nmodes, idx, n, col.p, threads);
             std::memset(col.p + nnz, 0, (stride - (size_t)nnz) * 4);
-            if ((e = cudaMemcpy(t->coo + (size_t)n * stride, col.p, stride * 4, cudaMemcpyHostToDevice)) !=
-                cudaSuccess)
-                return bail(cuda_fail(e, "device copy of the caller-order coordinates"));
+            if ((e = cudaMemcpy(t->coo + (size_t)n * stride, col.p, stride * 4, cudaMemcpyDefault)) != cudaSuccess)
+                return bail(cuda_fail(e, "copy of the caller-order coordinates"));
         }
     }
     amped_status s = ensure_scratch(t, max_rank);

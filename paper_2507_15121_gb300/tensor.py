@@ -38,12 +38,15 @@ class Tensor:
 
     ``idx`` is int32 [nnz, N] (0-based), ``vals`` float32 [nnz]; both host
     arrays (numpy or CPU torch).  Construction builds one output-row-ordered,
-    segmented copy per mode on the device (paper Sec. 3); it is synchronous.
+    segmented copy per mode (paper Sec. 3); it is synchronous.  With
+    ``stream_memory="host"`` the per-nonzero streams of the copies stay in
+    pinned host memory and the kernels read them over the host link
+    (out-of-core); factors, outputs and row tables are always on the device.
     """
 
     def __init__(self, dims, idx, vals, *, segment_items: int = 0, keep_perm: bool = True, keep_coo: bool = True,
                  max_rank: int = 0, host_threads: int = 0, inner_order: str = "lexicographic",
-                 short_rows: int = 0):
+                 short_rows: int = 0, stream_memory: str = "device"):
         L = _lib.lib()
         self.dims = tuple(int(d) for d in dims)
         idx = np.ascontiguousarray(idx.numpy() if hasattr(idx, "numpy") else idx, dtype=np.int32)
@@ -54,8 +57,10 @@ class Tensor:
         dims_a = np.asarray(self.dims, dtype=np.int64)
         if inner_order not in ("lexicographic", "stable"):
             raise ValueError("inner_order must be 'lexicographic' or 'stable'")
+        if stream_memory not in ("device", "host"):
+            raise ValueError("stream_memory must be 'device' or 'host'")
         opts = _lib.Opts(segment_items, 1 if keep_perm else 2, 1 if keep_coo else 2, max_rank, host_threads,
-                         2 if inner_order == "lexicographic" else 1, short_rows)
+                         2 if inner_order == "lexicographic" else 1, short_rows, 2 if stream_memory == "host" else 1)
         h = ctypes.c_void_p()
         _lib.check(L.amped_tensor_create(self.nnz, len(self.dims), dims_a.ctypes.data,
                                          idx.ctypes.data if self.nnz else None,

@@ -328,6 +328,39 @@ def test_fused_completion_grad_bf16_and_autograd():
 
 
 # --------------------------------------------------------------------------- full size, sampled rows
+@pytest.mark.parametrize("name,scale", [("zipf3", 0.002), ("zipf5", 0.0002)])
+def test_host_resident_streams_match_device(name, scale):
+    """Out-of-core form: the per-nonzero streams in mapped pinned host memory, read by the
+    same kernels over the host link, give the same bits as device-resident streams."""
+    w = synth.WORKLOADS[name].scaled(scale)
+    c = synth.make(w)
+    R = 16
+    F = [dev(f) for f in synth.factors(c.dims, R, w.seed)]
+    g = torch.from_numpy(np.random.default_rng(3).standard_normal(c.nnz).astype(np.float32)).cuda()
+    res = {}
+    for where in ("device", "host"):
+        t = amped.Tensor(c.dims, c.idx, c.vals, stream_memory=where)
+        outs = t.mttkrp_all(F)
+        m = t.cp_sample(F)
+        grads = t.cp_grad(F, g)
+        fg, loss = t.completion_grad(F)
+        A = [f.clone() for f in F]
+        grams = torch.empty((c.nmodes, R, R), dtype=torch.float64, device="cuda")
+        stats = torch.zeros(8, dtype=torch.float64, device="cuda")
+        t.cp_als_sweep(A, grams, stats, init=True)
+        torch.cuda.synchronize()
+        res[where] = ([o.cpu() for o in outs], m.cpu(), [x.cpu() for x in grads], [x.cpu() for x in fg],
+                      loss.item(), [a.cpu() for a in A], stats.cpu())
+        t.close()
+    d, h = res["device"], res["host"]
+    for a, b in zip(d[0] + [d[1]] + d[2] + d[3], h[0] + [h[1]] + h[2] + h[3]):
+        assert torch.equal(a, b)  # deterministic kernels, same data: identical bits
+    assert h[4] == pytest.approx(d[4], rel=1e-12)  # fp64 loss, atomics in any order
+    for a, b in zip(d[5], h[5]):
+        torch.testing.assert_close(b, a, rtol=1e-5, atol=1e-7)  # fp64 Gram atomics feed the solve
+    assert h[6][0].item() == pytest.approx(d[6][0].item(), abs=1e-9)
+
+
 def oracle_rows_all_modes(c, F, rows):
     """The oracle's sampled-row pass for every mode; the single-threaded passes of
     different modes run side by side (ctypes releases the GIL during each call)."""

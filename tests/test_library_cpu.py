@@ -63,6 +63,13 @@ def test_argument_errors_without_gpu(L):
     assert b"nonzero 1" in L.amped_last_error()
     neg = np.array([[0, -1]], dtype=np.int32)
     assert _create(L, 1, (3, 2), neg, vals[:1])[0] == _lib.ERR_INDEX
+    # stream_memory must be 0, 1 or 2 (checked before anything is allocated)
+    opts = _lib.Opts(0, 0, 0, 0, 0, 0, 0, 3)
+    dims_a = np.asarray((3, 2), dtype=np.int64)
+    h = ctypes.c_void_p()
+    assert L.amped_tensor_create(2, 2, dims_a.ctypes.data, idx.ctypes.data, vals.ctypes.data, ctypes.byref(opts),
+                                 ctypes.byref(h)) == _lib.ERR_INVALID
+    assert b"stream_memory" in L.amped_last_error()
     # calls on a NULL handle fail cleanly
     assert L.amped_mttkrp(None, 0, None, 0, 32, None, None) == _lib.ERR_INVALID
     assert L.amped_tensor_destroy(None) == _lib.OK
