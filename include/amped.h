@@ -116,7 +116,7 @@ amped_status amped_tensor_info(amped_tensor_t t, int64_t* nnz, int* nmodes, int6
  *   factors  host array of N device pointers; factors[n] is [dims[n]][R] in `fdtype`;
  *            factors[mode] is not read and may be NULL
  *   R        rank, 1..256 for fp32 and 1..512 for bf16/fp16 (R > 32 needs R % 8 == 0 for fp32,
- *            R % 16 == 0 for 16-bit); tensors of 2 to 5 modes
+ *            R % 16 == 0 for 16-bit); tensors of 2 to 8 modes
  *   out      device [dims[mode]][R] fp32, fully overwritten (rows without nonzeros become 0)
  * Enqueues a scratch reset, the persistent MTTKRP kernel and the split-row combine on `stream`.
  */
@@ -199,7 +199,7 @@ amped_status amped_tensor_norm2(amped_tensor_t t, double* norm2);
  *          a multiple of 8), updated in place.
  * grams:   device [N][R][R] fp64; on entry the Grams of the factors (or pass AMPED_ALS_INIT to
  *          compute them), on return those of the updated factors.
- * stats:   device [8] fp64.  1 <= R <= 64 (R > 32 a multiple of 8); 2 to 5 modes.
+ * stats:   device [8] fp64.  1 <= R <= 64 (R > 32 a multiple of 8); 2 to 8 modes.
  * The MTTKRP output and the solve's result live in workspace the handle allocates on first use
  * (dims_max x R fp32).  Asynchronous: read stats after synchronising the stream.
  */

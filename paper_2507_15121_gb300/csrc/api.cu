@@ -273,8 +273,9 @@ amped_status check_call(amped_tensor* t, const void* const* factors, amped_dtype
         if (!aligned(factors[n], al)) return fail(AMPED_ERR_INVALID, "factor %d is not %zu-byte aligned", n, al);
     }
     if (t->N < 2 && skip_mode >= 0) return AMPED_OK;
-    if (t->N - 1 > 4 && skip_mode >= 0)
-        return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 5 modes, tensor has %d", t->N);
+    if (t->N - 1 > kMaxIn && skip_mode >= 0)
+        return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to %d modes, tensor has %d", kMaxIn + 1,
+                    t->N);
     return AMPED_OK;
 }
 
@@ -532,7 +533,7 @@ amped_status amped_mttkrp_all(amped_tensor_t t, const void* const* factors, ampe
     int vec = 0;
     amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
     if (s != AMPED_OK) return s;
-    if (t->N - 1 > 4) return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 5 modes");
+    if (t->N - 1 > kMaxIn) return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to %d modes", kMaxIn + 1);
     for (int n = 0; n < t->N; ++n)
         if (!outs[n]) return fail(AMPED_ERR_INVALID, "output for mode %d is NULL", n);
     for (int n = 0; n < t->N; ++n) {
@@ -603,7 +604,8 @@ amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped
     int vec = 0;
     amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
     if (s != AMPED_OK) return s;
-    if (t->N < 2 || t->N > 5) return fail(AMPED_ERR_UNSUPPORTED, "sampled-model kernels are built for 2 to 5 modes");
+    if (t->N < 2 || t->N > AMPED_MAX_MODES)
+        return fail(AMPED_ERR_UNSUPPORTED, "sampled-model kernels are built for 2 to %d modes", AMPED_MAX_MODES);
     if (t->nnz == 0) return AMPED_OK;
     if (!m_out || !aligned(m_out, 16)) return fail(AMPED_ERR_INVALID, "m_out is NULL or not 16-byte aligned");
     SampleParams p{};
@@ -637,7 +639,7 @@ amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_d
     int vec = 0;
     amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
     if (s != AMPED_OK) return s;
-    if (t->N - 1 > 4) return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to 5 modes");
+    if (t->N - 1 > kMaxIn) return fail(AMPED_ERR_UNSUPPORTED, "MTTKRP kernels are built for 2 to %d modes", kMaxIn + 1);
     for (int n = 0; n < t->N; ++n)
         if (!grads[n]) return fail(AMPED_ERR_INVALID, "gradient %d is NULL", n);
     for (int n = 0; n < t->N; ++n) {
@@ -704,7 +706,8 @@ amped_status amped_cp_completion_grad(amped_tensor_t t, const void* const* facto
     int vec = 0;
     amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
     if (s != AMPED_OK) return s;
-    if (t->N < 2 || t->N - 1 > 4) return fail(AMPED_ERR_UNSUPPORTED, "completion kernels are built for 2 to 5 modes");
+    if (t->N < 2 || t->N - 1 > kMaxIn)
+        return fail(AMPED_ERR_UNSUPPORTED, "completion kernels are built for 2 to %d modes", kMaxIn + 1);
     for (int n = 0; n < t->N; ++n)
         if (!grads[n]) return fail(AMPED_ERR_INVALID, "gradient %d is NULL", n);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -736,7 +739,7 @@ amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, 
     if (flags & ~AMPED_ALS_INIT) return fail(AMPED_ERR_INVALID, "unknown flags 0x%x", flags);
     if (R < 1) return fail(AMPED_ERR_INVALID, "rank R=%d must be >= 1", R);
     if (R > als_max_rank()) return fail(AMPED_ERR_UNSUPPORTED, "CP-ALS is built for ranks up to %d", als_max_rank());
-    if (t->N < 2 || t->N - 1 > 4) return fail(AMPED_ERR_UNSUPPORTED, "CP-ALS is built for 2 to 5 modes");
+    if (t->N < 2 || t->N - 1 > kMaxIn) return fail(AMPED_ERR_UNSUPPORTED, "CP-ALS is built for 2 to %d modes", kMaxIn + 1);
     const void* cf[AMPED_MAX_MODES];
     for (int n = 0; n < t->N; ++n) cf[n] = factors[n];
     int vec = 0;

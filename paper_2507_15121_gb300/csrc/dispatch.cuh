@@ -10,6 +10,7 @@
 
 namespace amped {
 
+constexpr int kCarveoutPercentWide = 60;  // 32-byte records (4+ input modes): 4 blocks x 32 KB
 constexpr int kCarveoutPercent = 30;  // ~68 KB of the 228 KB shared-memory maximum: 4 blocks x 16 KB
 
 template <typename K>
@@ -48,7 +49,8 @@ static int launch_mttkrp_shape(const MttkrpParams& p, int grid_cap, cudaStream_t
         // The kernel needs little shared memory (the staged stream batches);
         // ask for the smallest carveout so the rest of the SM's 256 KB stays L1
         // cache for the factor-row gathers.
-        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, kCarveoutPercent);
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             NIN > 3 ? kCarveoutPercentWide : kCarveoutPercent);
         grid = blocks_per_sm(k) * device_sms();
     }
     int g = grid;
@@ -79,6 +81,9 @@ static int launch_mttkrp_nin(int nin, int lpn, const MttkrpParams& p, int grid_c
         case 2: return launch_mttkrp_lpn<T, VEC, 2, RES>(lpn, p, grid_cap, st);
         case 3: return launch_mttkrp_lpn<T, VEC, 3, RES>(lpn, p, grid_cap, st);
         case 4: return launch_mttkrp_lpn<T, VEC, 4, RES>(lpn, p, grid_cap, st);
+        case 5: return launch_mttkrp_lpn<T, VEC, 5, RES>(lpn, p, grid_cap, st);
+        case 6: return launch_mttkrp_lpn<T, VEC, 6, RES>(lpn, p, grid_cap, st);
+        case 7: return launch_mttkrp_lpn<T, VEC, 7, RES>(lpn, p, grid_cap, st);
         default: return (int)cudaErrorInvalidValue;
     }
 }
@@ -127,6 +132,9 @@ static int launch_sample_nm(int lpn, const SampleParams& p, cudaStream_t st) {
         case 3: return launch_sample_lpn<T, VEC, 3>(lpn, p, st);
         case 4: return launch_sample_lpn<T, VEC, 4>(lpn, p, st);
         case 5: return launch_sample_lpn<T, VEC, 5>(lpn, p, st);
+        case 6: return launch_sample_lpn<T, VEC, 6>(lpn, p, st);
+        case 7: return launch_sample_lpn<T, VEC, 7>(lpn, p, st);
+        case 8: return launch_sample_lpn<T, VEC, 8>(lpn, p, st);
         default: return (int)cudaErrorInvalidValue;
     }
 }
@@ -142,17 +150,21 @@ static int launch_sample_t(const SampleParams& p, cudaStream_t st) {
 
 }  // namespace amped
 
-// One translation unit per dtype defines these three with its own T.
+// Two translation units per dtype (compiled in parallel): the MTTKRP and
+// sampled-model launchers, and the residual (completion-gradient) launcher.
 #define AMPED_DEFINE_DTYPE_LAUNCHERS(T, SUFFIX)                                                               \
     namespace amped {                                                                                       \
     int launch_mttkrp_##SUFFIX(int nin, const MttkrpParams& p, int grid_cap, void* st) {                    \
         return launch_mttkrp_t<T, false>(nin, p, grid_cap, static_cast<cudaStream_t>(st));                 \
     }                                                                                                       \
-    int launch_residual_##SUFFIX(int nin, const MttkrpParams& p, int grid_cap, void* st) {                  \
-        return launch_mttkrp_t<T, true>(nin, p, grid_cap, static_cast<cudaStream_t>(st));                  \
-    }                                                                                                       \
     int launch_sample_##SUFFIX(const SampleParams& p, void* st) {                                           \
         return launch_sample_t<T>(p, static_cast<cudaStream_t>(st));                                        \
     }                                                                                                       \
     int vec_##SUFFIX(int R) { return Shape<T>::vec(R); }                                                    \
+    }
+#define AMPED_DEFINE_DTYPE_RESIDUAL_LAUNCHER(T, SUFFIX)                                                       \
+    namespace amped {                                                                                       \
+    int launch_residual_##SUFFIX(int nin, const MttkrpParams& p, int grid_cap, void* st) {                  \
+        return launch_mttkrp_t<T, true>(nin, p, grid_cap, static_cast<cudaStream_t>(st));                  \
+    }                                                                                                       \
     }

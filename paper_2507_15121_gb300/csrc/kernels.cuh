@@ -356,9 +356,9 @@ __device__ __forceinline__ void load_out_row(const MttkrpParams& p, int row, int
 // Steps per chunk: all gathers of a chunk are issued before any use.  Four
 // steps at 64 registers (4 blocks of 256 threads per SM) measured fastest on
 // GB300 for R = 32 (fp32 and bf16) against 2 or 8 steps at 2-4 blocks per SM.
-template <int VEC>
-struct Chunk {
-    static constexpr int value = VEC >= 8 ? 2 : 4;
+template <int VEC, int NIN>
+struct Chunk {  // nonzeros per group per fast-path step (fewer for 5+ input modes: registers)
+    static constexpr int value = VEC >= 8 ? (NIN >= 5 ? 1 : 2) : (NIN >= 5 ? 2 : 4);
 };
 
 constexpr int kBatch = 128;  // nonzeros per stream batch of a warp (32 lanes x 4)
@@ -406,29 +406,29 @@ __device__ __forceinline__ void prefetch_batch(const MttkrpParams& p, int kb, in
 // once per 128 bytes.
 __device__ __forceinline__ int swz(int j) { return j ^ ((j >> 3) & 7); }
 
-template <int NIN>
-struct Rec {
+template <int NIN, bool WIDE = (NIN > 3)>
+struct Rec {  // up to three input coordinates and the value: 16 bytes
     int4 a;
     __device__ __forceinline__ int idx(int n) const { return n == 0 ? a.x : n == 1 ? a.y : a.z; }
     __device__ __forceinline__ float val() const { return __int_as_float(a.w); }
 };
-template <>
-struct Rec<4> {
+template <int NIN>
+struct Rec<NIN, true> {  // four to seven input coordinates, then the value: 32 bytes
     int4 a, b;
-    __device__ __forceinline__ int idx(int n) const { return comp_rt(a, n); }
-    __device__ __forceinline__ float val() const { return __int_as_float(b.x); }
+    __device__ __forceinline__ int idx(int n) const { return n < 4 ? comp_rt(a, n) : comp_rt(b, n - 4); }
+    __device__ __forceinline__ float val() const { return __int_as_float(comp_rt(b, NIN - 4)); }
 };
 
-template <int NIN>
+template <int NIN, bool WIDE = (NIN > 3)>
 struct WarpStage {
     int4 a[kBatch];
     __device__ __forceinline__ Rec<NIN> get(int j) const { return Rec<NIN>{a[swz(j)]}; }
 };
-template <>
-struct WarpStage<4> {
+template <int NIN>
+struct WarpStage<NIN, true> {
     int4 a[kBatch];
     int4 b[kBatch];
-    __device__ __forceinline__ Rec<4> get(int j) const { return Rec<4>{a[swz(j)], b[swz(j)]}; }
+    __device__ __forceinline__ Rec<NIN> get(int j) const { return Rec<NIN>{a[swz(j)], b[swz(j)]}; }
 };
 
 template <int NIN>
@@ -446,7 +446,12 @@ __device__ __forceinline__ void stage_batch(WarpStage<NIN>& st, int lane, const 
         } else {
             st.a[slot] = make_int4(comp_rt(b.idx[0], c), comp_rt(b.idx[1], c), comp_rt(b.idx[2], c),
                                    comp_rt(b.idx[3], c));
-            st.b[slot] = make_int4(__float_as_int(comp_rt(b.val, c)), 0, 0, 0);
+            int w[4];
+#pragma unroll
+            for (int n = 4; n < 8; ++n)  // coordinates 4.., then the value, then zeros
+                w[n - 4] = n < NIN ? comp_rt(b.idx[n < NIN ? n : 0], c)
+                                   : (n == NIN ? __float_as_int(comp_rt(b.val, c)) : 0);
+            st.b[slot] = make_int4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -462,7 +467,7 @@ template <typename T, int VEC, int LPN, int NIN, bool RES>
 __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, WarpStage<NIN>& st, int lane,
                                                const T* const (&fl)[NIN], double& lsum) {
     constexpr int G = 32 / LPN;
-    constexpr int CH = Chunk<VEC>::value;
+    constexpr int CH = Chunk<VEC, NIN>::value;
     constexpr int CHN = CH * G;  // nonzeros per chunk
     static_assert(kBatch % CHN == 0, "a chunk must tile the batch");
     const int g = lane / LPN, q = lane % LPN;

@@ -84,7 +84,22 @@ def check_fit_terms(dims, idx, vals, A, lam, st):
     return 1.0 - np.sqrt(res) / np.sqrt(xx)
 
 
+class _Adhoc:  # seeded uniform tensors of 6 and 8 modes
+    def __init__(self, dims, nnz, seed):
+        rng = np.random.default_rng(seed)
+        self.dims, self.seed = dims, seed
+        self.idx = np.stack([rng.integers(0, d, nnz) for d in dims], axis=1).astype(np.int32)
+        self.vals = rng.uniform(0.1, 1.0, nnz).astype(np.float32)
+        self.nnz, self.nmodes = nnz, len(dims)
+
+
 def workload(name, scale=None):
+    if name == "six":
+        c = _Adhoc((60, 40, 30, 20, 12, 10), 30000, 61)
+        return c, c
+    if name == "eight":
+        c = _Adhoc((30, 25, 20, 16, 12, 10, 8, 6), 30000, 81)
+        return c, c
     w = synth.WORKLOADS[name]
     if scale is not None:
         w = w.scaled(scale)
@@ -92,6 +107,7 @@ def workload(name, scale=None):
 
 
 CASES = [("uniform3", None, 16), ("zipf3", 0.0005, 32), ("zipf4", 0.0001, 32), ("zipf5", 0.0002, 16),
+         ("six", None, 8), ("eight", None, 4),
          ("zipf3", 0.0002, 8), ("zipf3", 0.0002, 20), ("zipf3", 0.0002, 40), ("zipf3", 0.0002, 64),
          ("zipf3", 0.0002, 3)]
 

@@ -328,6 +328,44 @@ def test_fused_completion_grad_bf16_and_autograd():
 
 
 # --------------------------------------------------------------------------- full size, sampled rows
+@pytest.mark.parametrize("dims,R,dt", [((40, 30, 20, 12, 9, 7), 16, torch.float32),
+                                         ((30, 20, 15, 10, 8, 6, 5), 32, torch.float32),
+                                         ((25, 20, 12, 10, 8, 6, 5, 4), 8, torch.float32),
+                                         ((30, 20, 15, 10, 8, 6, 5), 32, torch.bfloat16),
+                                         ((25, 20, 12, 10, 8, 6, 5, 4), 3, torch.float32)])
+def test_six_to_eight_modes(dims, R, dt):
+    """Tensors of 6 to 8 modes (5 to 7 input modes per MTTKRP): every mode, the sampled
+    model, the gradient and the fused completion gradient against the oracle."""
+    rng = np.random.default_rng(len(dims) * 100 + R)
+    nnz = 20000
+    idx = np.stack([rng.integers(0, d, nnz) for d in dims], axis=1).astype(np.int32)
+    idx[: nnz // 4, 0] = 3  # one long row in mode 0
+    vals = rng.uniform(0, 1, nnz).astype(np.float32)
+    F32 = [rng.uniform(0, 1, (d, R)).astype(np.float32) for d in dims]
+    t = amped.Tensor(dims, idx, vals)
+    Fd = [dev(f, dt) for f in F32]
+    F = F32 if dt == torch.float32 else [host_bits(f) for f in Fd]
+    code = "f32" if dt == torch.float32 else "bf16"
+    outs = t.mttkrp_all(Fd)
+    m = t.cp_sample(Fd)
+    g = (m - torch.from_numpy(vals).cuda()).contiguous()
+    grads = t.cp_grad(Fd, g)
+    fg, loss = t.completion_grad(Fd)
+    torch.cuda.synchronize()
+    for n in range(len(dims)):
+        ref = oracle.mttkrp(dims, idx, vals, F, n, code)
+        assert oracle.row_error(outs[n].cpu().numpy(), ref) <= FP32_BAR, n
+    m_ref = oracle.cp_sample(dims, idx, F, code)
+    assert np.max(np.abs(m.cpu().numpy() - m_ref) / np.abs(m_ref)) <= FP32_BAR
+    g_ref = oracle.cp_grad(dims, idx, g.cpu().numpy().astype(np.float64), F, code)
+    x_ref = oracle.cp_grad(dims, idx, m_ref - vals.astype(np.float64), F, code)
+    for n in range(len(dims)):
+        assert oracle.row_error(grads[n].cpu().numpy(), g_ref[n], floor_frac=1e-6) <= GRAD_BAR, n
+        assert oracle.row_error(fg[n].cpu().numpy(), x_ref[n], floor_frac=1e-6) <= GRAD_BAR, n
+    assert loss.item() == pytest.approx(oracle.completion_loss(m_ref, vals), rel=1e-5)
+    t.close()
+
+
 @pytest.mark.parametrize("name,scale", [("zipf3", 0.002), ("zipf5", 0.0002)])
 def test_host_resident_streams_match_device(name, scale):
     """Out-of-core form: the per-nonzero streams in mapped pinned host memory, read by the
