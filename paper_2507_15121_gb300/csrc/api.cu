@@ -133,6 +133,9 @@ struct amped_tensor {
     int* als_info = nullptr;    // CP-ALS: solve status
     int als_rcap = 0;
     bool host_streams = false;      // per-nonzero streams in mapped pinned host memory
+    void* up_stream = nullptr;      // amped_mttkrp_all_host: upload and download streams and events
+    void* down_stream = nullptr;
+    void* copy_ev[AMPED_MAX_MODES + 4] = {};
     std::vector<void*> allocs;
     std::vector<void*> host_allocs;
 
@@ -163,6 +166,10 @@ struct amped_tensor {
         return cudaHostGetDevicePointer(p, h, 0);
     }
     ~amped_tensor() {
+        for (void* e : copy_ev)
+            if (e) cudaEventDestroy(static_cast<cudaEvent_t>(e));
+        if (up_stream) cudaStreamDestroy(static_cast<cudaStream_t>(up_stream));
+        if (down_stream) cudaStreamDestroy(static_cast<cudaStream_t>(down_stream));
         for (void* p : allocs) cudaFree(p);
         for (void* p : host_allocs) cudaFreeHost(p);
     }
@@ -189,6 +196,27 @@ cudaError_t upload_stream(amped_tensor* t, T** dst, const T* src, size_t n, size
     if (e == cudaSuccess && cap > n && !t->host_streams)  // host streams start zeroed
         e = cudaMemset(*dst + n, 0, (cap - n) * sizeof(T));
     return e;
+}
+
+// Streams and events for the overlapped copies of amped_mttkrp_all_host, created on first use.
+cudaError_t ensure_copy_streams(amped_tensor* t) {
+    if (t->up_stream) return cudaSuccess;
+    cudaStream_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking);
+    for (int i = 0; e == cudaSuccess && i < AMPED_MAX_MODES + 4; ++i) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        t->copy_ev[i] = ev;
+    }
+    if (e != cudaSuccess) {
+        if (a) cudaStreamDestroy(a);
+        if (b) cudaStreamDestroy(b);
+        return e;
+    }
+    t->up_stream = a;
+    t->down_stream = b;
+    return cudaSuccess;
 }
 
 // Scratch for the split-row partials, sized for rank R.
@@ -578,20 +606,39 @@ amped_status amped_mttkrp_all_host(amped_tensor_t t, const void* const* factors,
                 return cuda_fail(e, "staging allocation");
             t->stage_out_bytes[n] = ob;
         }
-        if ((e = cudaMemcpyAsync(t->stage_fac[n], factors[n], fb, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return cuda_fail(e, "factor upload");
         dfac[n] = t->stage_fac[n];
         dout[n] = t->stage_out[n];
     }
+    // Copies overlap the kernels: the factors mode 0 needs go first, factor 0 is uploaded
+    // while mode 0 runs, and each output is downloaded while the next mode runs.
+    if ((e = ensure_copy_streams(t)) != cudaSuccess) return cuda_fail(e, "copy streams");
+    cudaStream_t up = static_cast<cudaStream_t>(t->up_stream), down = static_cast<cudaStream_t>(t->down_stream);
+    cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(t->copy_ev);  // [0] entry, [1] rest in, [2] factor 0 in,
+                                                                  // [3 + m] output m ready, [3 + N] outputs out
+    auto upload = [&](int n) {
+        const size_t fb = (size_t)t->dims[n] * R * esize(fdtype);
+        return cudaMemcpyAsync(t->stage_fac[n], factors[n], fb, cudaMemcpyHostToDevice, up);
+    };
+    if ((e = cudaEventRecord(ev[0], st)) != cudaSuccess || (e = cudaStreamWaitEvent(up, ev[0], 0)) != cudaSuccess)
+        return cuda_fail(e, "copy ordering");
+    for (int n = 1; n < t->N; ++n)
+        if ((e = upload(n)) != cudaSuccess) return cuda_fail(e, "factor upload");
+    if ((e = cudaEventRecord(ev[1], up)) != cudaSuccess || (e = upload(0)) != cudaSuccess ||
+        (e = cudaEventRecord(ev[2], up)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ev[1], 0)) != cudaSuccess)
+        return cuda_fail(e, "factor upload");
     for (int n = 0; n < t->N; ++n) {
+        if (n == 1 && (e = cudaStreamWaitEvent(st, ev[2], 0)) != cudaSuccess) return cuda_fail(e, "copy ordering");
         s = run_mode(t, n, dfac, fdtype, R, vec, dout[n], nullptr, st);
         if (s != AMPED_OK) return s;
-    }
-    for (int n = 0; n < t->N; ++n) {
+        if ((e = cudaEventRecord(ev[3 + n], st)) != cudaSuccess || (e = cudaStreamWaitEvent(down, ev[3 + n], 0)) != cudaSuccess)
+            return cuda_fail(e, "copy ordering");
         const size_t ob = (size_t)t->dims[n] * R * 4;
-        if ((e = cudaMemcpyAsync(outs[n], dout[n], ob, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        if ((e = cudaMemcpyAsync(outs[n], dout[n], ob, cudaMemcpyDeviceToHost, down)) != cudaSuccess)
             return cuda_fail(e, "output download");
     }
+    if (t->N == 1 && (e = cudaStreamWaitEvent(st, ev[2], 0)) != cudaSuccess) return cuda_fail(e, "copy ordering");
+    if ((e = cudaEventRecord(ev[3 + t->N], down)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ev[3 + t->N], 0)) != cudaSuccess)
+        return cuda_fail(e, "copy ordering");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "host MTTKRP");
     return AMPED_OK;
 }
