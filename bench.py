@@ -61,15 +61,17 @@ def parse():
 
 
 # --------------------------------------------------------------------------- distributed plumbing
-def dist_setup(args):
+def dist_setup(args, backend=None):
+    """(world, rank, local rank, process group or None) from the torchrun
+    environment.  Ranks are independent replicas: the group carries only the
+    start/stop barriers and the max over ranks of the elapsed time."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
         import torch.distributed as dist
-        backend = "nccl" if args.impl == "ours" else "gloo"
-        dist.init_process_group(backend)
+        dist.init_process_group(backend or ("nccl" if args.impl == "ours" else "gloo"))
         pg = dist
     return world, rank, local, pg
 
@@ -488,10 +490,12 @@ def run_completion(args, w, world, rank, local, pg):
 def main():
     args = parse()
     w = synth.WORKLOADS[args.workload].scaled(args.scale)
+    if args.impl == "reference":  # rank 0 alone times the oracle; other ranks exit without work
+        world, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
+        run_reference(args, w, world, rank, None)
+        return
     world, rank, local, pg = dist_setup(args)
-    if args.impl == "reference":
-        run_reference(args, w, world, rank, pg)
-    elif w.planted_rank:
+    if w.planted_rank:
         run_completion(args, w, world, rank, local, pg)
     else:
         run_ours(args, w, world, rank, local, pg)
