@@ -174,6 +174,13 @@ amped_status amped_cp_completion_grad(amped_tensor_t t, const void* const* facto
  */
 amped_status amped_tensor_norm2(amped_tensor_t t, double* norm2);
 
+/*
+ * Host-only: the same ||X||^2 computed from host arrays without a GPU (the norm amped_tensor_create
+ * stores).  inner_order as in amped_opts (0 = default); *norm2 is a host double.
+ */
+amped_status amped_norm2_host(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, const float* vals,
+                              int inner_order, double* norm2);
+
 /* amped_cp_als_sweep flag: compute grams[n] = A_n^T A_n of the given factors before the sweep. */
 #define AMPED_ALS_INIT 1
 

@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
             "amped_plan_mode": ([i64, c_int, vp, vp, c_int, c_int, c_int, c_int, ctypes.POINTER(PlanSizes)]
                                 + [vp] * 9, st),
             "amped_tensor_norm2": ([vp, ctypes.POINTER(ctypes.c_double)], st),
+            "amped_norm2_host": ([i64, c_int, vp, vp, vp, c_int, ctypes.POINTER(ctypes.c_double)], st),
             "amped_cp_als_sweep": ([vp, vp, c_int, vp, vp, c_int, vp], st),
             "amped_cp_als_normalize": ([vp, vp, c_int, vp, vp, vp], st),
             "amped_set_kernel_events": ([vp, vp, vp], st),

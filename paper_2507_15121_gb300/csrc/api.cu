@@ -745,6 +745,28 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
     return AMPED_OK;
 }
 
+amped_status amped_norm2_host(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, const float* vals,
+                              int inner_order, double* norm2) {
+    g_err.clear();
+    if (!norm2) return fail(AMPED_ERR_INVALID, "norm2 is NULL");
+    if (nmodes < 1 || nmodes > AMPED_MAX_MODES || !dims || nnz < 0 || nnz > (int64_t)INT32_MAX - 4 * kPad)
+        return fail(AMPED_ERR_INVALID, "bad tensor shape");
+    for (int n = 0; n < nmodes; ++n)
+        if (dims[n] < 1 || dims[n] > (int64_t)INT32_MAX - 4 * kPad)
+            return fail(AMPED_ERR_INVALID, "dims[%d]=%lld out of range", n, (long long)dims[n]);
+    if (nnz > 0 && (!idx || !vals)) return fail(AMPED_ERR_INVALID, "idx or vals is NULL");
+    const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, 0);
+    if (bad >= 0) return fail(AMPED_ERR_INDEX, "nonzero %lld has a coordinate outside dims", (long long)bad);
+    HostMode hm;
+    const bool inner_sort = inner_order != 1;
+    if (!order_mode(nnz, nmodes, dims, idx, 0, inner_sort, 0, hm))
+        return fail(AMPED_ERR_OOM, "host allocation failed");
+    const double v = norm2_merged(hm, nmodes, idx, vals, inner_sort ? inner_mode(nmodes, dims, 0) : -1, 0);
+    if (v < 0.0) return fail(AMPED_ERR_OOM, "host allocation failed");
+    *norm2 = v;
+    return AMPED_OK;
+}
+
 amped_status amped_cp_completion_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
                                       float* const* grads, double* loss, void* stream) {
     g_err.clear();

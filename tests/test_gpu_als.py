@@ -229,3 +229,58 @@ def test_argument_errors():
     with pytest.raises(ValueError):  # wrong Gram shape
         t.cp_als_sweep([f[:, :32].contiguous() for f in F], grams, stats)
     t.close()
+
+
+@pytest.mark.slow
+def test_zipf3_full_size_sweep_sampled_rows():
+    """One CP-ALS sweep on the 200M-nonzero zipf3 tensor at R=32 (the configuration the
+    benchmark times).  For every mode the oracle recomputes the least-squares update of 2048
+    seeded rows (plus the 16 hottest) from the inputs that mode saw: its MTTKRP rows
+    (one pass over the COO) times V^-1 from fp64 Grams of those inputs.  The GPU keeps the
+    update unnormalised, so rows compare directly.  Also: every kept Gram against the Gram
+    of the stored factor, and <X, X^> against the oracle's sampled model over all nonzeros."""
+    import concurrent.futures as cf
+    w = synth.WORKLOADS["zipf3"]
+    c = synth.make(w)
+    R = 32
+    F = synth.factors(c.dims, R, w.seed)
+    t = amped.Tensor(c.dims, c.idx, c.vals)
+    Fd = to_dev(F)
+    grams = torch.empty((3, R, R), dtype=torch.float64, device="cuda")
+    stats = torch.zeros(8, dtype=torch.float64, device="cuda")
+    t.cp_als_sweep(Fd, grams, stats, init=True)
+    torch.cuda.synchronize()
+    Ag = [f.cpu().numpy() for f in Fd]
+    Gg, st = grams.cpu().numpy(), stats.cpu().numpy()
+    del Fd
+    t.close()
+    counts = [np.bincount(c.idx[:, m], minlength=c.dims[m]) for m in range(3)]
+    rows = [np.unique(np.concatenate([np.argsort(-counts[m], kind="stable")[:16],
+                                      synth.subset(c.dims[m], 2048, w.seed + m)])) for m in range(3)]
+    inputs = [[Ag[k] if k < n else F[k] for k in range(3)] for n in range(3)]
+    with cf.ThreadPoolExecutor(max_workers=3) as ex:
+        futs = [ex.submit(oracle.mttkrp_rows, c.dims, c.idx, c.vals, inputs[n], n, rows[n]) for n in range(3)]
+        M = [f.result() for f in futs]
+    for n in range(3):
+        G = [als.gram(a) for a in inputs[n]]
+        V = als.hadamard_others(G, n)
+        bar = 4 * np.linalg.cond(V) * (EPS_M + R * 2.0 ** -24)
+        ref = M[n] @ np.linalg.inv(V)
+        got = Ag[n][rows[n]].astype(np.float64)
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= bar, (n, err, bar)
+        Gs = als.gram(Ag[n])
+        assert np.abs(Gg[n] - Gs).max() <= 1e-6 * np.abs(Gs).max(), n
+    # <X, X^> over all 200M nonzeros: the oracle's sampled model in parallel slices
+    chunks = np.array_split(np.arange(c.nnz), 16)
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        parts = list(ex.map(lambda ix: float(np.dot(c.vals[ix].astype(np.float64),
+                                                    oracle.cp_sample(c.dims, c.idx[ix], Ag))), chunks))
+    xy = sum(parts)
+    W = np.ones((R, R))
+    for a in Ag:
+        W = W * als.gram(a)
+    yy = float(W.sum())
+    assert abs(st[3] - xy) <= TERM_BAR * (st[2] + yy), (st[3], xy)
+    assert abs(st[4] - yy) <= TERM_BAR * (st[2] + yy), (st[4], yy)
+    assert st[5] == 0 and 0.9 < st[0] < 1.0

@@ -235,3 +235,34 @@ def test_plan_empty_tensor_and_zipf():
     c = synth.make(w)
     for mode in range(3):
         check_plan(c.dims, c.idx, mode, 256)
+
+
+def _norm2_host(L, dims, idx, vals, inner_order):
+    dims_a = np.asarray(dims, dtype=np.int64)
+    out = ctypes.c_double()
+    rc = L.amped_norm2_host(idx.shape[0], len(dims), dims_a.ctypes.data, idx.ctypes.data if idx.size else None,
+                            vals.ctypes.data if vals.size else None, inner_order, ctypes.byref(out))
+    return rc, out.value
+
+
+@pytest.mark.parametrize("dims", [(30, 20, 10), (12, 9, 8, 5), (40, 30), (6, 5, 4, 3, 3, 2)])
+@pytest.mark.parametrize("inner_order", [0, 1, 2])
+def test_tensor_norm_sums_repeated_coordinates(L, dims, inner_order):
+    """The host norm ||X||^2 with repeated coordinates summed (the ALS fit's ||X||) equals the
+    oracle's, for every inner order, with many repeats (some rows hold most of the nonzeros)."""
+    from oracle import als
+    rng = np.random.default_rng(len(dims) * 10 + inner_order)
+    nnz = 3000
+    idx = np.stack([rng.integers(0, d, nnz) for d in dims], axis=1).astype(np.int32)
+    idx[: nnz // 3, 0] = 2  # a hot row
+    idx[nnz // 2:] = idx[rng.integers(0, nnz // 2, nnz - nnz // 2)]  # repeated coordinates
+    vals = rng.uniform(-1, 1, nnz).astype(np.float32)
+    rc, v = _norm2_host(L, dims, idx, vals, inner_order)
+    assert rc == _lib.OK
+    assert v == pytest.approx(als.norm2(idx, vals), rel=1e-12)
+    assert v != pytest.approx(float(np.dot(vals.astype(np.float64), vals)), rel=1e-3)  # repeats matter here
+    rc, v0 = _norm2_host(L, dims, idx[:0], vals[:0], inner_order)
+    assert rc == _lib.OK and v0 == 0.0
+    bad = idx.copy()
+    bad[5, 0] = dims[0]
+    assert _norm2_host(L, dims, bad, vals, inner_order)[0] == _lib.ERR_INDEX
