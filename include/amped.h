@@ -4,16 +4,19 @@
  * The library computes sparse MTTKRP along every mode of an N-mode COO
  * tensor (paper Sec. 2.1 Eq. 1: X_(d) times the Khatri-Rao product of the
  * other factors), which is the bottleneck of CP decomposition, together with
- * the sampled CP model and its gradient for gradient-based CP completion.
- * Everything runs on one GPU.  There is no CPU fallback: a call either
- * enqueues CUDA kernels or returns an error.
+ * the sampled CP model and its gradient for gradient-based CP completion, and
+ * CP decomposition by alternating least squares around the MTTKRP.  Everything
+ * runs on one GPU.  There is no CPU fallback: a call either enqueues CUDA
+ * kernels or returns an error (amped_plan_mode and amped_norm2_host are
+ * host-only queries).
  *
  * Conventions shared by all entry points
  *  - Indices are 0-based int32; nnz < 2^31; 1 <= nmodes <= AMPED_MAX_MODES;
  *    every dims[n] >= 1 and < 2^31.
  *  - Factors are dense row-major [dims[n]][R] device arrays in fp32, bf16 or
- *    fp16 (`amped_dtype`), base address aligned to 16 bytes.  Products and
- *    sums are always fp32; outputs are fp32.
+ *    fp16 (`amped_dtype`), base address aligned to 16 bytes (32 bytes when R
+ *    is a multiple of 8 (fp32) or 16 (16-bit)).  Products and sums are always
+ *    fp32; outputs are fp32.
  *  - Device buffers passed in (factors, outputs, values) are owned by the
  *    caller and must stay valid until the work enqueued on `stream` is done.
  *    The handle owns every device copy it builds and frees it in
