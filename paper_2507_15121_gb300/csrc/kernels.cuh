@@ -747,8 +747,16 @@ __device__ __forceinline__ void mttkrp_short(const MttkrpParams& p, int t, WarpS
     __syncwarp();  // the stage is reused by the warp's next segment
 }
 
+// Resident blocks per SM the residual-mode kernel is compiled for: as many as
+// fit without heavy spilling (it needs the output-mode row, the gathered
+// Khatri-Rao row and the accumulator per lane).
+template <typename T, int VEC, int NIN>
+constexpr int res_blocks() {
+    return VEC == 1 ? 4 : (sizeof(T) == 2 ? 2 : (NIN <= 2 ? 4 : 3));
+}
+
 template <typename T, int VEC, int LPN, int NIN, bool RES>
-__global__ void __launch_bounds__(256, RES ? 2 : 4) mttkrp_kernel(const MttkrpParams p) {
+__global__ void __launch_bounds__(256, RES ? res_blocks<T, VEC, NIN>() : 4) mttkrp_kernel(const MttkrpParams p) {
     __shared__ __align__(16) WarpStage<NIN> stage[8];
     const int lane = threadIdx.x & 31;
     WarpStage<NIN>& st = stage[threadIdx.x >> 5];
