@@ -353,11 +353,14 @@ __device__ __forceinline__ void load_out_row(const MttkrpParams& p, int row, int
 }
 
 // ------------------------------------------------------------------ MTTKRP
-// Steps per chunk: all gathers of a chunk are issued before any use.  Four
-// steps at 64 registers (4 blocks of 256 threads per SM) measured fastest on
-// GB300 for R = 32 (fp32 and bf16) against 2 or 8 steps at 2-4 blocks per SM.
+// Steps per chunk (nonzeros per group per fast-path chunk): all gathers of a
+// chunk are issued before any use.  The 256-bit vector shapes hold a 32-byte
+// slice of every gathered row in registers, so they take 2 steps at 64
+// registers (4 blocks of 256 threads per SM); on GB300 at R = 32 that beat 4
+// steps at 3 blocks per SM by 3-4 %.  Scalar shapes take 4; 5+ input modes
+// take half as many (registers).
 template <int VEC, int NIN>
-struct Chunk {  // nonzeros per group per fast-path step (fewer for 5+ input modes: registers)
+struct Chunk {
     static constexpr int value = VEC >= 8 ? (NIN >= 5 ? 1 : 2) : (NIN >= 5 ? 2 : 4);
 };
 
