@@ -1,5 +1,9 @@
 """GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
 
+Also: tensors of 2 to 8 modes, host-resident (out-of-core) streams against
+device-resident ones (identical bits), the end-to-end host-buffer entry, and
+full-size runs checked on sampled rows.
+
 Bars: fp32 factors -> max relative row error <= 1e-5; bf16/fp16 factors ->
 <= 1e-5 against the oracle run on the same rounded factors (kernel
 arithmetic) and <= 2e-2 against the oracle on the original fp32 factors
