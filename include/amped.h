@@ -217,6 +217,16 @@ amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, 
                                 int flags, void* stream);
 
 /*
+ * One CP-ALS mode update (the step amped_cp_als_sweep repeats for d = 0 .. N-1): the mode-`mode`
+ * MTTKRP, the fp64 solve against the Hadamard product of the other Grams, factors[mode] replaced by
+ * the unnormalised least-squares update and grams[mode] by its Gram; stats as for a sweep, for the
+ * model after this update (stats[5..6] count this update only).  Same arguments and flags as
+ * amped_cp_als_sweep, plus the mode.
+ */
+amped_status amped_cp_als_update(amped_tensor_t t, int mode, float* const* factors, int R, double* grams,
+                                 double* stats, int flags, void* stream);
+
+/*
  * Normalised form of a CP model [[A_0, ..., A_{N-1}]] = [[lambda; B_0, ..., B_{N-1}]]: every
  * factor's columns scaled to unit 2-norm in place (a zero column stays zero), lambda_r = product
  * over n of the column norms (device [R] fp32), and grams (device [N][R][R] fp64, the Grams of the

@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
             "amped_norm2_host": ([i64, c_int, vp, vp, vp, c_int, ctypes.POINTER(ctypes.c_double)], st),
             "amped_cp_als_sweep": ([vp, vp, c_int, vp, vp, c_int, vp], st),
             "amped_cp_als_normalize": ([vp, vp, c_int, vp, vp, vp], st),
+            "amped_cp_als_update": ([vp, c_int, vp, c_int, vp, vp, c_int, vp], st),
             "amped_set_kernel_events": ([vp, vp, vp], st),
             "amped_kernel_launches": ([], i64),
             "amped_last_error": ([], ctypes.c_char_p),

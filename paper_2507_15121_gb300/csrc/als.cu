@@ -11,7 +11,8 @@
 //   apply_kernel   A_d = M W stored (fp32, 4x4 register tiles, packed f32x2
 //                  FMA); the same pass accumulates the Gram of the stored
 //                  A_d and ip_r = sum_i M(i,r) A_d(i,r)
-//   finish_kernel  one block: commits the new Gram; after the last mode, the fit
+//   finish_kernel  one block: commits the new Gram; the fit when asked (after a
+//                  sweep's last mode, or after a single update)
 //   gram_kernel    A^T A of the starting factors (first sweep only)
 //   normalize      on request: unit-norm columns, lambda = product of the norms
 //

@@ -161,9 +161,9 @@ struct AlsParams {
     double* ga;          // [R][R] Gram of the stored update, then (contiguous) ...
     double* ip;          // [R] ... sum_i M(i,r) A(i,r) of the stored update (workspace)
     int* info;           // 0, or the first failed Cholesky pivot + 1
-    double* stats;       // [8] fit terms (written after the last mode), failure counters
+    double* stats;       // [8] fit terms (written when `last` is set), failure counters
     double xnorm2;       // ||X||^2
-    int32_t N, mode, R, last;
+    int32_t N, mode, R, last;  // last: compute the fit terms of the model after this update
 };
 int als_max_rank();
 // G = A^T A (fp64; G is zeroed first) of a row-major [rows][R] fp32 matrix.

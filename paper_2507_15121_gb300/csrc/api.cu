@@ -800,53 +800,94 @@ amped_status amped_tensor_norm2(amped_tensor_t t, double* norm2) {
     return AMPED_OK;
 }
 
-amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, double* grams, double* stats,
-                                int flags, void* stream) {
-    g_err.clear();
+}  // extern "C"
+
+namespace {
+
+// Argument checks shared by the CP-ALS entry points; fills cf and vec.
+amped_status als_check(amped_tensor* t, float* const* factors, int R, const double* grams, const double* stats,
+                       int flags, const void** cf, int* vec) {
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (!factors || !grams || !stats) return fail(AMPED_ERR_INVALID, "factors, grams or stats is NULL");
     if (flags & ~AMPED_ALS_INIT) return fail(AMPED_ERR_INVALID, "unknown flags 0x%x", flags);
     if (R < 1) return fail(AMPED_ERR_INVALID, "rank R=%d must be >= 1", R);
     if (R > als_max_rank()) return fail(AMPED_ERR_UNSUPPORTED, "CP-ALS is built for ranks up to %d", als_max_rank());
     if (t->N < 2 || t->N - 1 > kMaxIn) return fail(AMPED_ERR_UNSUPPORTED, "CP-ALS is built for 2 to %d modes", kMaxIn + 1);
-    const void* cf[AMPED_MAX_MODES];
     for (int n = 0; n < t->N; ++n) cf[n] = factors[n];
-    int vec = 0;
-    amped_status s = check_call(t, cf, AMPED_F32, R, -1, &vec);
+    amped_status s = check_call(t, cf, AMPED_F32, R, -1, vec);
     if (s != AMPED_OK) return s;
     for (int n = 0; n < t->N; ++n)
         if (!aligned(factors[n], 16)) return fail(AMPED_ERR_INVALID, "factor %d is not 16-byte aligned", n);
     if (!aligned(grams, 8) || !aligned(stats, 8)) return fail(AMPED_ERR_INVALID, "grams or stats is misaligned");
-    if ((s = ensure_als(t, R)) != AMPED_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return ensure_als(t, R);
+}
+
+// Optional starting Grams, then the failure counters reset.
+amped_status als_begin(amped_tensor* t, float* const* factors, int R, double* grams, double* stats, int flags,
+                       cudaStream_t st) {
     int launched = 0, rc = 0;
     if (flags & AMPED_ALS_INIT)
-        for (int n = 0; n < t->N && rc == 0; ++n) rc = launch_gram(factors[n], t->dims[n], R, grams + (size_t)n * R * R, st, &launched);
+        for (int n = 0; n < t->N && rc == 0; ++n)
+            rc = launch_gram(factors[n], t->dims[n], R, grams + (size_t)n * R * R, st, &launched);
     if (rc == 0) rc = (int)cudaMemsetAsync(stats + 5, 0, 2 * sizeof(double), st);
     g_launches += launched;
-    if (rc != 0) return cuda_fail((cudaError_t)rc, "CP-ALS initial Grams");
-    for (int m = 0; m < t->N; ++m) {
-        s = run_mode(t, m, cf, AMPED_F32, R, vec, t->als_m, nullptr, st);
-        if (s != AMPED_OK) return s;
-        launched = 0;
-        AlsParams p{};
-        p.grams = grams;
-        p.ga = t->als_gm;
-        p.ip = p.ga + (size_t)R * R;
-        p.w = t->als_w;
-        p.info = t->als_info;
-        p.stats = stats;
-        p.xnorm2 = t->xnorm2;
-        p.N = t->N;
-        p.mode = m;
-        p.R = R;
-        p.last = m == t->N - 1;
-        rc = launch_als_solve(p, st, &launched);
-        if (rc == 0) rc = launch_als_apply(p, t->als_m, t->dims[m], factors[m], st, &launched);
-        g_launches += launched;
-        if (rc != 0) return cuda_fail((cudaError_t)rc, "CP-ALS kernel launch");
-    }
+    return rc ? cuda_fail((cudaError_t)rc, "CP-ALS initial Grams") : AMPED_OK;
+}
+
+// One mode: MTTKRP, fp64 solve, apply with the Gram fused, commit; the fit
+// terms of the resulting model when `fit` is set.
+amped_status als_mode(amped_tensor* t, int m, float* const* factors, const void* const* cf, int R, int vec,
+                      double* grams, double* stats, bool fit, cudaStream_t st) {
+    amped_status s = run_mode(t, m, cf, AMPED_F32, R, vec, t->als_m, nullptr, st);
+    if (s != AMPED_OK) return s;
+    int launched = 0;
+    AlsParams p{};
+    p.grams = grams;
+    p.ga = t->als_gm;
+    p.ip = p.ga + (size_t)R * R;
+    p.w = t->als_w;
+    p.info = t->als_info;
+    p.stats = stats;
+    p.xnorm2 = t->xnorm2;
+    p.N = t->N;
+    p.mode = m;
+    p.R = R;
+    p.last = fit;
+    int rc = launch_als_solve(p, st, &launched);
+    if (rc == 0) rc = launch_als_apply(p, t->als_m, t->dims[m], factors[m], st, &launched);
+    g_launches += launched;
+    return rc ? cuda_fail((cudaError_t)rc, "CP-ALS kernel launch") : AMPED_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, double* grams, double* stats,
+                                int flags, void* stream) {
+    g_err.clear();
+    const void* cf[AMPED_MAX_MODES];
+    int vec = 0;
+    amped_status s = als_check(t, factors, R, grams, stats, flags, cf, &vec);
+    if (s != AMPED_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((s = als_begin(t, factors, R, grams, stats, flags, st)) != AMPED_OK) return s;
+    for (int m = 0; m < t->N; ++m)
+        if ((s = als_mode(t, m, factors, cf, R, vec, grams, stats, m == t->N - 1, st)) != AMPED_OK) return s;
     return AMPED_OK;
+}
+
+amped_status amped_cp_als_update(amped_tensor_t t, int mode, float* const* factors, int R, double* grams,
+                                 double* stats, int flags, void* stream) {
+    g_err.clear();
+    const void* cf[AMPED_MAX_MODES];
+    int vec = 0;
+    amped_status s = als_check(t, factors, R, grams, stats, flags, cf, &vec);
+    if (s != AMPED_OK) return s;
+    if (mode < 0 || mode >= t->N) return fail(AMPED_ERR_INVALID, "mode %d outside 0..%d", mode, t->N - 1);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((s = als_begin(t, factors, R, grams, stats, flags, st)) != AMPED_OK) return s;
+    return als_mode(t, mode, factors, cf, R, vec, grams, stats, true, st);
 }
 
 amped_status amped_cp_als_normalize(amped_tensor_t t, float* const* factors, int R, double* grams, float* lambda,

@@ -220,6 +220,14 @@ class Tensor:
         _lib.check(_lib.lib().amped_cp_als_sweep(self.handle, fp, R, grams.data_ptr(), stats.data_ptr(),
                                                  _lib.ALS_INIT if init else 0, _stream_ptr(stream)))
 
+    def cp_als_update(self, mode: int, factors, grams, stats, init: bool = False, stream=None) -> None:
+        """One CP-ALS mode update: factors[mode] becomes the unnormalised
+        least-squares update after the mode-`mode` MTTKRP; grams[mode] its
+        Gram; stats the fit terms of the resulting model."""
+        fp, R = self._als_buffers(factors, grams, stats)
+        _lib.check(_lib.lib().amped_cp_als_update(self.handle, int(mode), fp, R, grams.data_ptr(), stats.data_ptr(),
+                                                  _lib.ALS_INIT if init else 0, _stream_ptr(stream)))
+
     def cp_als_normalize(self, factors, grams, lam=None, stream=None):
         """Scale every factor's columns to unit norm in place; returns lambda
         (the products of the norms) and rescales `grams`."""

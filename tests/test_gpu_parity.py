@@ -27,11 +27,14 @@ GRAD_BAR = 1e-4
 
 
 def dev(a, dtype=torch.float32):
-    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+    # rounded to the storage type on the host, then uploaded: the device holds the same bits
+    # that host_bits() gives the oracle
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).to("cuda")
 
 
 def host_bits(t):
-    """raw uint16 bit patterns of a bf16/fp16 CUDA tensor (oracle input)."""
+    """raw uint16 bit patterns of a bf16/fp16 tensor made by dev() (oracle input: the host
+    rounding, read back unchanged)."""
     return t.detach().cpu().view(torch.int16).numpy().view(np.uint16)
 
 
@@ -352,16 +355,16 @@ def test_six_to_eight_modes(dims, R, dt):
     code = "f32" if dt == torch.float32 else "bf16"
     outs = t.mttkrp_all(Fd)
     m = t.cp_sample(Fd)
-    g = (m - torch.from_numpy(vals).cuda()).contiguous()
-    grads = t.cp_grad(Fd, g)
+    m_ref = oracle.cp_sample(dims, idx, F, code)
+    g = (m_ref - vals.astype(np.float64)).astype(np.float32)  # residuals of the oracle's model
+    grads = t.cp_grad(Fd, torch.from_numpy(g).cuda())
     fg, loss = t.completion_grad(Fd)
     torch.cuda.synchronize()
     for n in range(len(dims)):
         ref = oracle.mttkrp(dims, idx, vals, F, n, code)
         assert oracle.row_error(outs[n].cpu().numpy(), ref) <= FP32_BAR, n
-    m_ref = oracle.cp_sample(dims, idx, F, code)
     assert np.max(np.abs(m.cpu().numpy() - m_ref) / np.abs(m_ref)) <= FP32_BAR
-    g_ref = oracle.cp_grad(dims, idx, g.cpu().numpy().astype(np.float64), F, code)
+    g_ref = oracle.cp_grad(dims, idx, g.astype(np.float64), F, code)
     x_ref = oracle.cp_grad(dims, idx, m_ref - vals.astype(np.float64), F, code)
     for n in range(len(dims)):
         assert oracle.row_error(grads[n].cpu().numpy(), g_ref[n], floor_frac=1e-6) <= GRAD_BAR, n
