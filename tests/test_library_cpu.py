@@ -202,6 +202,8 @@ CASES = [
     ("hypersparse", (5000, 7, 3), 40, 3),
     ("four-modes", (12, 9, 8, 5), 500, 4),
     ("two-modes", (40, 30), 250, 5),
+    ("six-modes", (9, 8, 7, 6, 5, 4), 400, 6),
+    ("eight-modes", (6, 5, 5, 4, 4, 3, 3, 2), 300, 7),
 ]
 
 
