@@ -201,6 +201,25 @@ def test_exact_low_rank_sparse_tensor_is_recovered():
     assert np.abs(m_g - vals).max() <= 1e-4 * np.abs(vals).max()
 
 
+@pytest.mark.parametrize("case", ["r1", "r2"])
+def test_hand_worked_update(case):
+    """The hand-worked fixture (tests/golden/tiny_als.txt) through amped_cp_als_update."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_oracle_als_pins import load_golden_als
+    g = load_golden_als()
+    c = g["cases"][case]
+    R = c["R"]
+    F = [np.ones((g["dims"][0], R)), np.array(c["A1"]), np.array(c["A2"])]
+    t = amped.Tensor(g["dims"], g["idx"], g["vals"].astype(np.float32))
+    A0, _, st = gpu_update(t, F, 0, R)
+    t.close()
+    np.testing.assert_allclose(A0, np.array(c["A0new"]), rtol=1e-6, atol=1e-7)
+    xx, xy, yy, res = c["terms"]
+    np.testing.assert_allclose([st[2], st[3], st[4], st[1]], [xx, xy, yy, res], rtol=1e-6)
+
+
 def test_singular_normal_equations_are_reported():
     w, c = workload("zipf3", 0.0002)
     R = 4

@@ -10,10 +10,14 @@ other than the oracle itself:
   point: fit 1, factors unchanged up to column scaling;
 * the dense residual never grows from one mode update to the next (each
   update is an exact least-squares step);
+* a hand-worked fixture (tests/golden/tiny_als.txt): two mode-0 updates and
+  the fit terms of the updated models, worked out by hand;
 * planted mistakes in the oracle (the mode's own Gram in V, a matrix
   product for the Hadamard product, repeated coordinates not summed, lam left
   out of the model) each fail one of these.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -202,3 +206,45 @@ def test_mttkrp_accepts_fp64_factors_exactly():
     got = oracle.mttkrp(dims, idx, vals, A, 0, "f64")
     ref = unfold(densify(dims, idx, vals), 0) @ kr_others(A, 0)
     np.testing.assert_allclose(got, ref, rtol=1e-13)
+
+
+# --- hand-worked fixture ------------------------------------------------------------------
+
+GOLDEN_ALS = os.path.join(os.path.dirname(__file__), "golden", "tiny_als.txt")
+
+
+def load_golden_als():
+    """{'dims', 'idx', 'vals', 'cases': {name: {'R', 'A1', 'A2', 'A0new', 'terms'}}}."""
+    g = {"idx": [], "vals": [], "cases": {}}
+    cur = None
+    for line in open(GOLDEN_ALS):
+        tok = line.split()
+        if not tok or tok[0].startswith("#"):
+            continue
+        if tok[0] == "dims":
+            g["dims"] = tuple(int(x) for x in tok[1:])
+        elif tok[0] == "nz":
+            g["idx"].append([int(x) for x in tok[1:-1]])
+            g["vals"].append(float(tok[-1]))
+        elif tok[0] == "case":
+            cur = g["cases"].setdefault(tok[1], {"R": int(tok[2]), "A1": [], "A2": [], "A0new": []})
+        elif tok[0] in ("A1", "A2", "A0new"):
+            cur[tok[0]].append([float(x) for x in tok[1:]])
+        elif tok[0] == "terms":
+            cur["terms"] = [float(x) for x in tok[1:]]
+    g["idx"] = np.array(g["idx"], dtype=np.int32)
+    g["vals"] = np.array(g["vals"])
+    return g
+
+
+@pytest.mark.parametrize("case", ["r1", "r2"])
+def test_golden_hand_worked_als(case):
+    g = load_golden_als()
+    c = g["cases"][case]
+    R = c["R"]
+    A1, A2, expect = np.array(c["A1"]), np.array(c["A2"]), np.array(c["A0new"])
+    A0_start = np.ones((g["dims"][0], R))  # not read by the mode-0 update
+    An, lam = als.update_mode(g["dims"], g["idx"], g["vals"], [A0_start, A1, A2], 0)
+    np.testing.assert_allclose(An * lam[None, :], expect, atol=1e-12)
+    xx, xy, yy = als.fit_terms(g["dims"], g["idx"], g["vals"], [expect, A1, A2], np.ones(R))
+    np.testing.assert_allclose([xx, xy, yy, xx - 2 * xy + yy], c["terms"], rtol=1e-12)
