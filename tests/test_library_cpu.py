@@ -40,6 +40,27 @@ def test_exports_every_declared_symbol(L):
     assert L.amped_version().decode().startswith("amped-gb300")
 
 
+def test_header_is_plain_c(tmp_path):
+    """The boundary header compiles as strict ISO C (no C++ or CUDA types leak into it), and a C
+    program that calls every declared entry point links against the library."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    names = declared_functions()
+    src = tmp_path / "use_amped.c"
+    src.write_text('#include "amped.h"\n#include <stdio.h>\ntypedef void (*fn_t)(void);\nint main(void) {\n'
+                   "    amped_opts o = {0};\n    (void)o;\n    fn_t fns[] = {\n"
+                   + "".join(f"        (fn_t){n},\n" for n in names)
+                   + '    };\n    printf("%d\\n", (int)(sizeof fns / sizeof fns[0]));\n'
+                   + "    return (int)AMPED_OK;\n}\n")
+    lib_dir = os.path.join(ROOT, "paper_2507_15121_gb300")
+    subprocess.check_call([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.dirname(HEADER),
+                           str(src), "-o", str(tmp_path / "use_amped"), "-L", lib_dir, "-lamped",
+                           f"-Wl,-rpath,{lib_dir}"])
+
+
 def _create(L, nnz, dims, idx, vals):
     dims_a = np.asarray(dims, dtype=np.int64)
     h = ctypes.c_void_p()
