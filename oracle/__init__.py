@@ -56,7 +56,7 @@ def _L():
         lib = ctypes.CDLL(build())
         i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
         lib.oracle_mttkrp.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32, i32, i32, vp]
-        lib.oracle_mttkrp_rows.argtypes = [i64, i32, vp, vp, vp, vp, i32, i32, i32, i64, vp, vp]
+        lib.oracle_mttkrp_rows.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32, i32, i32, i64, vp, vp]
         lib.oracle_cp_sample.argtypes = [i64, i32, vp, vp, vp, i32, i32, vp]
         lib.oracle_cp_grad.argtypes = [i64, i32, vp, vp, vp, vp, i32, i32, vp]
         for f in (lib.oracle_mttkrp, lib.oracle_mttkrp_rows, lib.oracle_cp_sample, lib.oracle_cp_grad):
@@ -109,12 +109,15 @@ def mttkrp(dims, idx, vals, factors, mode: int, dtype: str = "f32") -> np.ndarra
 
 
 def mttkrp_rows(dims, idx, vals, factors, mode: int, rows, dtype: str = "f32") -> np.ndarray:
-    """MTTKRP restricted to the (strictly increasing) output rows `rows`."""
+    """MTTKRP restricted to the (strictly increasing) output rows `rows`;
+    vals float32 or float64."""
     dims_a, idx, fs, fptrs, R = _common(dims, idx, factors, dtype)
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     out = np.empty((rows.shape[0], R), dtype=np.float64)
-    vals = np.ascontiguousarray(vals, dtype=np.float32)
-    _rc(_L().oracle_mttkrp_rows(idx.shape[0], len(dims_a), _ptr(dims_a), _ptr(idx), _ptr(vals), fptrs,
+    vals = np.ascontiguousarray(vals)
+    v32 = vals if vals.dtype == np.float32 else None
+    v64 = np.ascontiguousarray(vals, dtype=np.float64) if v32 is None else None
+    _rc(_L().oracle_mttkrp_rows(idx.shape[0], len(dims_a), _ptr(dims_a), _ptr(idx), _ptr(v32), _ptr(v64), fptrs,
                                 DTYPES[dtype], R, mode, rows.shape[0], _ptr(rows), _ptr(out)))
     return out
 

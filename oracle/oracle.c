@@ -93,13 +93,14 @@ int oracle_mttkrp(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* i
 }
 
 /*
- * The same sum restricted to a chosen set of output rows: rows[0..nrows) is
+ * The same sum restricted to a chosen set of output rows (values fp32 in vals32, or fp64 in
+ * vals64 when vals32 is NULL): rows[0..nrows) is
  * a strictly increasing list of mode-`mode` indices and out is [nrows][R].
  * A bitmap screens the nonzeros and a binary search finds the row's slot,
  * so a full-size tensor can be checked on a sample of its output rows.
  */
 int oracle_mttkrp_rows(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, const float* vals32,
-                       const void* const* factors, int dtype, int R, int mode, int64_t nrows,
+                       const double* vals64, const void* const* factors, int dtype, int R, int mode, int64_t nrows,
                        const int64_t* rows, double* out) {
     if (nnz < 0 || nmodes < 1 || R < 1 || mode < 0 || mode >= nmodes || nrows < 0) return -1;
     for (int64_t j = 0; j < nrows; ++j)
@@ -120,7 +121,7 @@ int oracle_mttkrp_rows(int64_t nnz, int nmodes, const int64_t* dims, const int32
             int64_t mid = (lo + hi) / 2;
             if (rows[mid] < i) lo = mid + 1; else hi = mid;
         }
-        double v = (double)vals32[k];
+        double v = vals32 ? (double)vals32[k] : vals64[k];
         for (int r = 0; r < R; ++r) ell[r] = v;
         for (int w = 0; w < nmodes; ++w) {
             if (w == mode) continue;

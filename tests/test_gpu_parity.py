@@ -467,3 +467,67 @@ def test_zipf4_billion_full_size_sampled_rows():
     refs = oracle_rows_all_modes(c, F, rows)
     for m in range(4):
         assert oracle.row_error(outs[m][rows[m]], refs[m]) <= FP32_BAR, m
+
+
+@pytest.mark.slow
+def test_zipf3_r64_full_size_16bit_sampled_rows():
+    """The precision configuration at full size: 10M x 5M x 2M, 200M nonzeros, R=64, factors
+    stored in bf16 and in fp16 (rounded on the host from the same fp32 draws).  2048 seeded
+    rows per mode (plus the 16 hottest): each 16-bit result against the oracle on its own
+    rounded factors (kernel arithmetic) and against the oracle on the fp32 factors."""
+    w = synth.WORKLOADS["zipf3_r64"]
+    c = synth.make(w)
+    F = synth.factors(c.dims, 64, w.seed)
+    rows = [sampled_rows(c, m, 2048, w.seed) for m in range(3)]
+    t = amped.Tensor(c.dims, c.idx, c.vals)
+    got, bits = {}, {}
+    for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        Fd = [dev(f, dt) for f in F]
+        bits[name] = [host_bits(f) for f in Fd]
+        got[name] = [o.cpu().numpy()[rows[m]] for m, o in enumerate(t.mttkrp_all(Fd))]
+        del Fd
+    t.close()
+    torch.cuda.empty_cache()
+    ref32 = oracle_rows_all_modes(c, F, rows)
+    for name in ("bf16", "f16"):
+        import concurrent.futures as cf
+        with cf.ThreadPoolExecutor(max_workers=3) as ex:
+            futs = [ex.submit(oracle.mttkrp_rows, c.dims, c.idx, c.vals, bits[name], m, rows[m], name)
+                    for m in range(3)]
+            ref16 = [f.result() for f in futs]
+        for m in range(3):
+            assert oracle.row_error(got[name][m], ref16[m]) <= FP32_BAR, (name, m)
+            assert oracle.row_error(got[name][m], ref32[m]) <= LOWP_BAR, (name, m)
+
+
+@pytest.mark.slow
+def test_planted3_full_size_fused_completion_gradient():
+    """The differentiation configuration at full size: 5M x 2M x 1M, 100M nonzeros drawn from
+    a planted rank-16 CP model plus N(0, 0.01^2) noise at Zipf positions, R=32 fp32 factors.
+    The fused loss against the oracle's over all 100M nonzeros, and 2048 seeded gradient rows
+    per mode (plus the 16 hottest) against the oracle's MTTKRP of its own residuals."""
+    import concurrent.futures as cf
+    w = synth.WORKLOADS["planted3"]
+    c = synth.make(w)
+    chunks = np.array_split(np.arange(c.nnz), 16)
+
+    def sample(F):  # the oracle's sampled model over all nonzeros, in parallel slices
+        with cf.ThreadPoolExecutor(max_workers=16) as ex:
+            return np.concatenate(list(ex.map(lambda ix: oracle.cp_sample(c.dims, c.idx[ix], F), chunks)))
+    x = (sample(c.extra["planted_factors"]) + c.extra["noise"]).astype(np.float32)
+    F = synth.factors(c.dims, 32, w.seed, scale=w.factor_scale)
+    t = amped.Tensor(c.dims, c.idx, x)
+    grads, loss = t.completion_grad([dev(f) for f in F])
+    rows = [sampled_rows(c, m, 2048, w.seed) for m in range(3)]
+    got = [g.cpu().numpy()[rows[m]] for m, g in enumerate(grads)]
+    loss = loss.item()
+    del grads
+    t.close()
+    torch.cuda.empty_cache()
+    r = sample(F) - x.astype(np.float64)  # the oracle's residuals
+    assert loss == pytest.approx(oracle.completion_loss(r + x, x), rel=1e-5)
+    with cf.ThreadPoolExecutor(max_workers=3) as ex:
+        futs = [ex.submit(oracle.mttkrp_rows, c.dims, c.idx, r, F, m, rows[m]) for m in range(3)]
+        refs = [f.result() for f in futs]
+    for m in range(3):
+        assert oracle.row_error(got[m], refs[m], floor_frac=1e-6) <= GRAD_BAR, m

@@ -185,6 +185,10 @@ def test_rows_subset_matches_full():
         full = oracle.mttkrp(c.dims, c.idx, c.vals, F, m)
         rows = synth.subset(c.dims[m], 50, seed=m)
         np.testing.assert_array_equal(oracle.mttkrp_rows(c.dims, c.idx, c.vals, F, m, rows), full[rows])
+        # fp64 values (residuals) take the same path
+        v64 = c.vals.astype(np.float64) - 0.5
+        full64 = oracle.mttkrp(c.dims, c.idx, v64, F, m)
+        np.testing.assert_array_equal(oracle.mttkrp_rows(c.dims, c.idx, v64, F, m, rows), full64[rows])
 
 
 def test_16bit_factor_widening_exact():
