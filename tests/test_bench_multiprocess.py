@@ -50,12 +50,13 @@ def test_max_over_ranks_and_barrier_with_gloo():
     assert res == [(0, 2, 2.5), (1, 2, 2.5)]  # every rank sees the slowest rank's time
 
 
-def test_reference_arm_under_torchrun_prints_once():
+def test_reference_arm_under_torchrun_prints_once(tmp_path):
     port = free_port()
+    env = dict(os.environ, TMPDIR=str(tmp_path))  # torchrun's scratch stays in the test's directory
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
            "--gpus", "2", "--steps", "1", "--warmup", "1", "--workload", "uniform3"]
-    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
