@@ -85,6 +85,9 @@ class _Adhoc:  # seeded uniform tensors of 6 and 8 modes
 
 
 def workload(name, scale=None):
+    if name == "two":
+        c = _Adhoc((300, 200), 20000, 21)
+        return c, c
     if name == "six":
         c = _Adhoc((60, 40, 30, 20, 12, 10), 30000, 61)
         return c, c
@@ -98,7 +101,7 @@ def workload(name, scale=None):
 
 
 CASES = [("uniform3", None, 16), ("zipf3", 0.0005, 32), ("zipf4", 0.0001, 32), ("zipf5", 0.0002, 16),
-         ("six", None, 8), ("eight", None, 4),
+         ("six", None, 8), ("eight", None, 4), ("two", None, 6),
          ("zipf3", 0.0002, 8), ("zipf3", 0.0002, 20), ("zipf3", 0.0002, 40), ("zipf3", 0.0002, 64),
          ("zipf3", 0.0002, 3)]
 

@@ -203,6 +203,13 @@ def test_repeat_calls_and_single_mode_entry():
     host = t.mttkrp_all_host([torch.from_numpy(f) for f in F])
     for m in range(3):
         np.testing.assert_array_equal(host[m].numpy(), b[m])
+    # 16-bit host factors (pinned, so the copies overlap the kernels) against the device entry
+    Fh = [torch.from_numpy(f).to(torch.bfloat16).pin_memory() for f in F]
+    outs_h = [torch.empty((d, 32), dtype=torch.float32).pin_memory() for d in c.dims]
+    t.mttkrp_all_host(Fh, outs_h)
+    dev_b = t.mttkrp_all([f.cuda() for f in Fh])
+    for m in range(3):
+        np.testing.assert_array_equal(outs_h[m].numpy(), dev_b[m].cpu().numpy())
     assert amped.kernel_launches() > 0
 
 
