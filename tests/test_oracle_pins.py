@@ -296,3 +296,115 @@ def test_pins_reject_mutants(mutant):
         ok.append(np.allclose(_loop_mttkrp(dims, idx, vals, F, m, mutant), ref, rtol=1e-9))
         assert np.allclose(_loop_mttkrp(dims, idx, vals, F, m, None), ref, rtol=1e-9)
     assert not all(ok), mutant
+
+
+# ----------------------------------------------------------------------------- the parity metric
+# oracle.row_error is the metric every GPU parity assertion goes through: the
+# max relative row error of the MTTKRP output (the row-wise reading of the
+# error bound on X_(d) times the Khatri-Rao product, Sec. 2.1 Eq. 1).  Its
+# cases are worked by hand, so a slip in the function (wrong axis, a missing
+# absolute value, a mean for the max, a lenient rule for empty rows, the
+# floor taken on the wrong side) changes at least one expected number.
+ROW_ERROR_CASES = [
+    # (gpu, ref, floor_frac, expected, what the case fixes)
+    ([[10.0, 0.2], [1.0, 1.0]], [[10.0, 0.1], [1.0, 1.0]], 0.0, 0.01,
+     "row 0: |0.2-0.1| / max(10, 0.1) = 0.01; row 1 exact; the max over rows is 0.01"),
+    ([[2.0, 3.0]], [[2.0, 4.0]], 0.0, 0.25, "gpu below ref: |3-4| / 4"),
+    ([[-3.0, 1.0]], [[-4.0, 1.0]], 0.0, 0.25, "negative reference entry: |(-3)-(-4)| / |-4|"),
+    ([[1.0, 1.0], [2.0, 5.0], [0.5, 0.5]], [[1.0, 1.0], [2.0, 4.0], [0.5, 0.25]], 0.0, 0.5,
+     "row 1: |5-4| / 4 = 0.25; row 2: |0.5-0.25| / 0.5 = 0.5; the max over rows is 0.5"),
+    ([[0.0, 0.0], [1.0, 1.5]], [[0.0, 0.0], [1.0, 1.0]], 0.0, 0.5, "empty row matched exactly is skipped"),
+    ([[0.0, 1e-30], [1.0, 1.0]], [[0.0, 0.0], [1.0, 1.0]], 0.0, float("inf"),
+     "any value in a row whose reference is empty is an error"),
+    ([[0.0, 0.0]], [[0.0, 0.0]], 0.0, 0.0, "all-zero reference matched exactly"),
+    ([[0.0, -2.0]], [[0.0, 0.0]], 0.0, float("inf"), "all-zero reference, nonzero result"),
+    ([[2e-9, -1e-9], [2.0, -1.0]], [[1e-9, -1e-9], [2.0, -1.0]], 0.0, 1.0,
+     "tiny mixed-sign row without a floor: 1e-9 / 1e-9"),
+    ([[2e-9, -1e-9], [2.0, -1.0]], [[1e-9, -1e-9], [2.0, -1.0]], 1e-6, 5e-4,
+     "with floor_frac 1e-6 the denominator is 1e-6 * max row norm 2 = 2e-6: 1e-9 / 2e-6"),
+    ([[0.0, 3e-6], [-4.0, 2.0]], [[0.0, 0.0], [-4.0, 2.0]], 1e-6, 3e-6 / 4e-6,
+     "the floor also covers an empty reference row: 3e-6 / (1e-6 * 4)"),
+]
+
+
+@pytest.mark.parametrize("case", range(len(ROW_ERROR_CASES)))
+def test_row_error_hand_worked(case):
+    gpu, ref, ff, expected, why = ROW_ERROR_CASES[case]
+    got = oracle.row_error(np.array(gpu), np.array(ref), floor_frac=ff)
+    if np.isinf(expected):
+        assert np.isinf(got), why
+    else:
+        assert got == pytest.approx(expected, rel=1e-12, abs=0.0), why
+
+
+def test_row_error_inputs_and_shapes():
+    # float32 inputs are widened before the difference (no fp32 rounding of the error)
+    a = np.array([[1.0 + 2 ** -23]], dtype=np.float32)
+    b = np.array([[1.0]], dtype=np.float64)
+    assert oracle.row_error(a, b) == pytest.approx(2 ** -23, rel=1e-12)
+    assert oracle.row_error(np.zeros((0, 4)), np.zeros((0, 4))) == 0.0
+    # symmetric in which rows are hit: the error of the worst row, wherever it is
+    rng = np.random.default_rng(5)
+    ref = rng.uniform(0.5, 1.0, (50, 8))
+    for r in (0, 17, 49):
+        gpu = ref.copy()
+        gpu[r, 3] *= 1 + 1e-3
+        assert oracle.row_error(gpu, ref) == pytest.approx(1e-3 * ref[r, 3] / ref[r].max(), rel=1e-9)
+
+
+# mutants of the metric, written here; each must give a different answer on some hand-worked case
+def _re_axis0(gpu, ref, floor_frac=0.0):
+    gpu, ref = np.asarray(gpu, float), np.asarray(ref, float)
+    num, den = np.abs(gpu - ref).max(axis=0), np.abs(ref).max(axis=0)
+    z = den == 0
+    return float("inf") if np.any(num[z] != 0) else (float((num[~z] / den[~z]).max()) if np.any(~z) else 0.0)
+
+
+def _re_no_abs(gpu, ref, floor_frac=0.0):
+    gpu, ref = np.asarray(gpu, float), np.asarray(ref, float)
+    num, den = (gpu - ref).max(axis=1), ref.max(axis=1)
+    if floor_frac > 0:
+        den = np.maximum(den, floor_frac * den.max())
+    z = den == 0
+    return float("inf") if np.any(num[z] != 0) else (float((num[~z] / den[~z]).max()) if np.any(~z) else 0.0)
+
+
+def _re_mean(gpu, ref, floor_frac=0.0):
+    gpu, ref = np.asarray(gpu, float), np.asarray(ref, float)
+    num, den = np.abs(gpu - ref).max(axis=1), np.abs(ref).max(axis=1)
+    if floor_frac > 0:
+        den = np.maximum(den, floor_frac * den.max())
+    z = den == 0
+    return float("inf") if np.any(num[z] != 0) else (float((num[~z] / den[~z]).mean()) if np.any(~z) else 0.0)
+
+
+def _re_lenient_empty(gpu, ref, floor_frac=0.0):
+    gpu, ref = np.asarray(gpu, float), np.asarray(ref, float)
+    num, den = np.abs(gpu - ref).max(axis=1), np.abs(ref).max(axis=1)
+    if floor_frac > 0:
+        den = np.maximum(den, floor_frac * den.max())
+    z = den == 0
+    return float((num[~z] / den[~z]).max()) if np.any(~z) else 0.0
+
+
+def _re_floor_min(gpu, ref, floor_frac=0.0):
+    gpu, ref = np.asarray(gpu, float), np.asarray(ref, float)
+    num, den = np.abs(gpu - ref).max(axis=1), np.abs(ref).max(axis=1)
+    if floor_frac > 0:
+        den = np.minimum(den, floor_frac * den.max())
+    z = den == 0
+    return float("inf") if np.any(num[z] != 0) else (float((num[~z] / den[~z]).max()) if np.any(~z) else 0.0)
+
+
+@pytest.mark.parametrize("mutant", [_re_axis0, _re_no_abs, _re_mean, _re_lenient_empty, _re_floor_min])
+def test_row_error_cases_reject_mutants(mutant, monkeypatch):
+    # the mutant stands in for the oracle's function; the hand-worked cases must notice
+    monkeypatch.setattr(oracle, "row_error", mutant)
+    caught = False
+    for gpu, ref, ff, expected, _ in ROW_ERROR_CASES:
+        got = oracle.row_error(np.array(gpu), np.array(ref), floor_frac=ff)
+        if np.isinf(expected) != np.isinf(got) or (not np.isinf(expected) and abs(got - expected) > 1e-12 * max(
+                1.0, abs(expected))):
+            caught = True
+            break
+    assert caught, mutant.__name__
