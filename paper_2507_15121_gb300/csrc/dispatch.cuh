@@ -6,9 +6,32 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace amped {
+
+constexpr int kMaxDevices = 64;
+
+// Launch state of one kernel instantiation, kept per device: the grid size
+// (resident blocks x SMs of that device) and whether the carveout attribute
+// has been set there.  Threads racing on the first launch compute the same
+// value, so a relaxed atomic store is enough.
+struct PerDeviceGrid {
+    std::atomic<int> grid[kMaxDevices];
+    template <class Init>
+    int get(Init init) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return init();
+        int g = grid[dev].load(std::memory_order_relaxed);
+        if (g == 0) {
+            g = init();
+            grid[dev].store(g, std::memory_order_relaxed);
+        }
+        return g;
+    }
+};
 
 constexpr int kCarveoutPercentWide = 60;  // 32-byte records (4+ input modes): 4 blocks x 32 KB
 constexpr int kCarveoutPercent = 30;  // ~68 KB of the 228 KB shared-memory maximum: 4 blocks x 16 KB
@@ -44,16 +67,15 @@ struct Shape {
 template <typename T, int VEC, int LPN, int NIN, bool RES>
 static int launch_mttkrp_shape(const MttkrpParams& p, int grid_cap, cudaStream_t st) {
     auto k = mttkrp_kernel<T, VEC, LPN, NIN, RES>;
-    static int grid = 0;  // persistent grid: every resident block slot on every SM
-    if (grid == 0) {
+    static PerDeviceGrid grid;  // persistent grid: every resident block slot on every SM
+    int g = grid.get([&] {
         // The kernel needs little shared memory (the staged stream batches);
         // ask for the smallest carveout so the rest of the SM's 256 KB stays L1
-        // cache for the factor-row gathers.
+        // cache for the factor-row gathers.  The attribute is per device.
         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                              NIN > 3 ? kCarveoutPercentWide : kCarveoutPercent);
-        grid = blocks_per_sm(k) * device_sms();
-    }
-    int g = grid;
+        return blocks_per_sm(k) * device_sms();
+    });
     if (grid_cap > 0 && g > grid_cap) g = grid_cap;
     k<<<g, 256, 0, st>>>(p);
     return (int)cudaGetLastError();
@@ -100,8 +122,8 @@ static int launch_mttkrp_t(int nin, const MttkrpParams& p, int grid_cap, cudaStr
 template <typename T, int VEC, int LPN, int NM>
 static int launch_sample_shape(const SampleParams& p, cudaStream_t st) {
     auto k = sample_kernel<T, VEC, LPN, NM>;
-    static int grid = 0;
-    if (grid == 0) grid = blocks_per_sm(k) * device_sms();
+    static PerDeviceGrid grids;
+    const int grid = grids.get([&] { return blocks_per_sm(k) * device_sms(); });
     const int64_t workers_needed = ((int64_t)p.nnz + 4 * LPN - 1) / (4 * LPN);
     int64_t g = (workers_needed * LPN + 255) / 256;
     if (g > grid) g = grid;
