@@ -65,8 +65,9 @@ typedef struct {
     int32_t max_rank;      /* rank the scratch is first sized for (grown on demand); default 64 */
     int32_t host_threads;  /* threads for the host reorder; 0 = all available */
     int32_t inner_order;   /* order of the nonzeros inside an output row: 1 = caller order (stable);
-                              2 = by the coordinate of the largest other mode (better reuse of that
-                              factor's rows); 0 = default (2) */
+                              2 = lexicographic in the other coordinates, the mode with the largest
+                              dimension most significant (ties: lower mode index), so consecutive
+                              nonzeros share factor rows the kernel keeps in registers; 0 = default (2) */
     int32_t short_rows;    /* rows with fewer nonzeros than this (at most 125) are "short": they are
                               sorted by length and processed one row per lane group; longer rows are
                               processed by whole warps along the merge path.  0 = default (32);
@@ -149,8 +150,11 @@ amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped
                              float* m_out, void* stream);
 
 /*
- * Gradient of a loss L(m) of the sampled model, given gvals[k] = dL/dm_k in caller order
- * (device [nnz] fp32):
+ * Gradient of a loss L(m) of the sampled model (the CP model of paper Sec. 2.1 read at the
+ * nonzeros), given gvals[k] = dL/dm_k in caller order (device [nnz] fp32).  By the chain rule
+ * dm_k/dA_n(i, r) is the product of the other modes' factor entries at nonzero k, so the gradient
+ * is the elementwise computation of paper Sec. 3 (Alg. 2) with each nonzero's value replaced by
+ * gvals[k]:
  *   grads[n](i, r) = sum over nonzeros k with i_n(k) = i of gvals[k] * prod_{w != n} A_w(i_w(k), r)
  * i.e. the mode-n MTTKRP with the values replaced by gvals, for every n.  grads: host array of N
  * device pointers [dims[n]][R] fp32, overwritten.  Needs opts.keep_perm.
@@ -267,7 +271,9 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
 
 /*
  * Size of the library's fixed device scratch buffer used by amped_mttkrp_noalloc (32 MiB).
- * Every GPU that loads the library reserves this much device memory until the process exits.
+ * It is reserved on a device when the first handle is created there (amped_tensor_create looks
+ * up the buffer's device address, which loads the module that holds it) and stays reserved
+ * until the process exits.
  */
 #define AMPED_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 
@@ -288,12 +294,14 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
  * tasks) returns AMPED_ERR_UNSUPPORTED without launching anything; use amped_mttkrp then, or a
  * larger segment_items at create time (fewer segments).
  *
- * The first call on each device looks up that device's address of the array
- * (cudaGetSymbolAddress, with the device current); make that first call before any stream
- * capture begins.  The array is shared by every handle and every call on the device and keeps
- * the last call's contents (the ticket counter is cleared on the call's stream before each
- * launch): calls that may overlap on the GPU (different streams, other threads) race on it, so
- * serialise them.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * Set-up: amped_tensor_create looks up the array's address on its device (cudaGetSymbolAddress,
+ * with that device current), once per device, so this call itself only reads the cached address.
+ * The device current at the call must be the handle's device (else AMPED_ERR_INVALID).  If that
+ * lookup failed at create time, this call returns AMPED_ERR_CUDA.  The array is shared by every
+ * handle and every call on the device and keeps the last call's contents (the ticket counter is
+ * cleared on the call's stream before each launch): calls that may overlap on the GPU (different
+ * streams, other threads) race on it, so serialise them.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  Honours amped_set_kernel_events like amped_mttkrp.
  */
 amped_status amped_mttkrp_noalloc(amped_tensor_t t, int mode, const void* const* factors, amped_dtype fdtype,
                                   int R, float* out, void* stream);
@@ -305,7 +313,11 @@ amped_status amped_set_kernel_events(amped_tensor_t t, void* start, void* stop);
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 int64_t amped_kernel_launches(void);
 
-/* Message describing the last error returned to the calling thread ("" if none). */
+/* Message describing the last error returned to the calling thread ("" if none).
+ * Fault injection for testing clean-up paths (host side only): with the environment variable
+ * AMPED_FAULT=alloc:K, the K-th device allocation (1-based) inside each entry-point call fails as
+ * if the device were out of memory; the call then frees what it built and returns AMPED_ERR_OOM.
+ * The variable is read at every allocation. */
 const char* amped_last_error(void);
 
 /* Library version string. */

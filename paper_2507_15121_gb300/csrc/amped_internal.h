@@ -76,11 +76,17 @@ int64_t find_bad_index(int64_t nnz, int nmodes, const int64_t* dims, const int32
 bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, int threads,
                HostMode& hm, const int32_t* order = nullptr);
 
-// The other mode whose coordinate orders nonzeros inside a row (largest dim), or -1.
-int inner_mode(int nmodes, const int64_t* dims, int mode);
-// Mode order: by i_mode, and inside a row by the inner mode's coordinate when
-// inner_sort is set (caller order otherwise); both stable.
-bool order_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, bool inner_sort,
+// Priority of the coordinates in the inner order: modes by decreasing
+// dimension, ties by increasing mode index (prio[0] is the most significant).
+void mode_priority(int nmodes, const int64_t* dims, int* prio);
+// Caller indices in lexicographic order of all N coordinates, most significant
+// (highest priority) first; ties keep caller order.  One stable counting sort
+// per mode, least significant first.  Returns false on allocation failure.
+bool lex_order(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int threads, HostBuf<int32_t>& out);
+// Mode order: by i_mode; inside a row in the order of `lex` (the lexicographic
+// order from lex_order, which orders a row by the other coordinates in priority
+// order), or in caller order when lex is null.  Stable.
+bool order_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, const int32_t* lex,
                 int threads, HostMode& hm);
 
 // Splits the rows into long rows (at least `threshold` nonzeros; threshold
@@ -105,12 +111,13 @@ void gather_values(const HostMode& hm, const float* vals, float* dst, int thread
 // Caller-order column: dst[k] = idx[k][mode].
 void caller_column(int64_t nnz, int nmodes, const int32_t* idx, int mode, int32_t* dst, int threads);
 
-// ||X||^2 with repeated coordinates summed into one entry, from the copy
-// ordered by order_mode (before classify_rows): runs of equal row (and equal
-// `inner` coordinate when inner >= 0) are sorted by the full coordinate so
-// repeats become adjacent.  fp64, the same result for any thread count.
-// Returns a negative value on allocation failure.
-double norm2_merged(const HostMode& hm, int nmodes, const int32_t* idx, const float* vals, int inner, int threads);
+// ||X||^2 with repeated coordinates summed into one entry, from a copy ordered
+// by order_mode (before classify_rows).  With lex_sorted (the copy follows the
+// lexicographic order) repeated coordinates are adjacent inside a row;
+// otherwise each row is sorted by the full coordinate first.  fp64, the same
+// result for any thread count.  Returns a negative value on allocation failure.
+double norm2_merged(const HostMode& hm, int nmodes, const int32_t* idx, const float* vals, bool lex_sorted,
+                    int threads);
 
 // ---------------------------------------------------------------------------
 // Device side.

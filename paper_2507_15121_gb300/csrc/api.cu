@@ -36,8 +36,15 @@ using namespace amped;
 namespace {
 
 thread_local std::string g_err;
+thread_local int64_t g_call_allocs = 0;  // device allocations made by the current entry-point call
 std::atomic<int64_t> g_launches{0};
-std::atomic<int64_t> g_allocs{0};
+
+// Start of every entry point: clear the thread's error message and restart
+// the per-call allocation count the fault injector uses.
+void begin_call() {
+    g_err.clear();
+    g_call_allocs = 0;
+}
 
 amped_status fail(amped_status s, const char* fmt, ...) {
     char buf[512];
@@ -55,14 +62,45 @@ amped_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 // Host-side fault injection for testing clean-up paths: AMPED_FAULT=alloc:K
-// makes the K-th device allocation of the process (1-based) report failure.
+// makes the K-th device allocation (1-based) inside each entry-point call
+// report failure, as cudaMalloc does when the device is out of memory.  The
+// variable is read at every allocation, so a test can arm and disarm it
+// between calls.
 int64_t fault_alloc_at() {
-    static const int64_t at = [] {
-        const char* s = std::getenv("AMPED_FAULT");
-        if (!s || std::strncmp(s, "alloc:", 6) != 0) return int64_t(0);
-        return (int64_t)std::atoll(s + 6);
-    }();
-    return at;
+    const char* s = std::getenv("AMPED_FAULT");
+    if (!s || std::strncmp(s, "alloc:", 6) != 0) return 0;
+    return (int64_t)std::atoll(s + 6);
+}
+
+// Scratch of amped_mttkrp_noalloc: one static device array per GPU.  Host
+// code must not use this name as an address (on the host it is only a
+// stand-in); the device address comes from cudaGetSymbolAddress, looked up
+// once per device by noalloc_resolve with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[AMPED_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+cudaError_t g_noalloc_err[kMaxDevices] = {};
+
+// Looks up the array's address on `dev` (the current device) once.  Called by
+// amped_tensor_create, so the array's module is loaded, and its memory
+// reserved, when the first handle on a device is built rather than inside an
+// allocation-free call.  A failed lookup is remembered and reported by
+// amped_mttkrp_noalloc; it does not fail the handle.
+void noalloc_resolve(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_addr[dev]) return;
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e == cudaSuccess && ptr) {
+        g_noalloc_addr[dev] = ptr;
+        g_noalloc_err[dev] = cudaSuccess;
+    } else {
+        g_noalloc_err[dev] = e == cudaSuccess ? cudaErrorInvalidSymbol : e;
+        cudaGetLastError();  // the failure is reported by the allocation-free call, not left pending
+    }
 }
 
 size_t esize(amped_dtype dt) { return dt == AMPED_F32 ? 4 : 2; }
@@ -94,15 +132,20 @@ struct DevMode {
     int slot_mode[AMPED_MAX_MODES] = {};  // input slot -> tensor mode; slot 0 is the inner-order mode
 };
 
-// Input slots of a mode copy: the mode that orders nonzeros inside a row first
-// (the kernel reuses its factor rows across consecutive nonzeros), then the
-// other modes in increasing order.
+// Input slots of a mode copy.  With the lexicographic inner order: the other
+// modes in priority order (decreasing dimension), which is the order the copy
+// sorts a row by, so slot 0 changes least often along a row and the kernel's
+// cached factor rows are reused longest.  Otherwise: increasing mode index.
 int input_slots(int nmodes, const int64_t* dims, int mode, bool inner_sort, int* slot_mode) {
+    int prio[AMPED_MAX_MODES];
+    if (inner_sort) {
+        mode_priority(nmodes, dims, prio);
+    } else {
+        for (int n = 0; n < nmodes; ++n) prio[n] = n;
+    }
     int nin = 0;
-    const int inner = inner_sort ? inner_mode(nmodes, dims, mode) : -1;
-    if (inner >= 0) slot_mode[nin++] = inner;
-    for (int n = 0; n < nmodes; ++n)
-        if (n != mode && n != inner) slot_mode[nin++] = n;
+    for (int p = 0; p < nmodes; ++p)
+        if (prio[p] != mode) slot_mode[nin++] = prio[p];
     return nin;
 }
 
@@ -141,7 +184,7 @@ struct amped_tensor {
 
     cudaError_t dalloc(void** p, size_t bytes) {
         *p = nullptr;
-        const int64_t n = ++g_allocs;
+        const int64_t n = ++g_call_allocs;
         const int64_t f = fault_alloc_at();
         if (f > 0 && n == f) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
@@ -158,6 +201,9 @@ struct amped_tensor {
     cudaError_t salloc(void** p, size_t bytes) {
         if (!host_streams) return dalloc(p, bytes);
         *p = nullptr;
+        const int64_t n = ++g_call_allocs;
+        const int64_t f = fault_alloc_at();
+        if (f > 0 && n == f) return cudaErrorMemoryAllocation;
         void* h = nullptr;
         cudaError_t e = cudaHostAlloc(&h, bytes ? bytes : 16, cudaHostAllocMapped | cudaHostAllocPortable);
         if (e != cudaSuccess) return e;
@@ -394,7 +440,7 @@ int64_t amped_kernel_launches(void) { return g_launches.load(); }
 
 amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
                                  const float* vals, const amped_opts* opts, amped_tensor_t* out) {
-    g_err.clear();
+    begin_call();
     if (!out) return fail(AMPED_ERR_INVALID, "output handle pointer is NULL");
     *out = nullptr;
     if (nmodes < 1 || nmodes > AMPED_MAX_MODES)
@@ -433,6 +479,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
     amped_tensor* t = new (std::nothrow) amped_tensor;
     if (!t) return fail(AMPED_ERR_OOM, "host allocation failed");
     cudaGetDevice(&t->device);
+    noalloc_resolve(t->device);
     if (items == 0) items = default_segment_items(nnz, nmodes, dims, t->device);
     t->N = nmodes;
     t->nnz = nnz;
@@ -449,12 +496,15 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
     HostBuf<float> fcol;
     if (!col.alloc(stride) || !fcol.alloc(stride)) return bail(fail(AMPED_ERR_OOM, "host allocation failed"));
     cudaError_t e;
+    HostBuf<int32_t> lex;  // lexicographic order of all coordinates; every mode's copy is a stable sort of it
+    if (inner_sort && !lex_order(nnz, nmodes, dims, idx, threads, lex))
+        return bail(fail(AMPED_ERR_OOM, "host allocation failed in the lexicographic order"));
     for (int mode = 0; mode < nmodes; ++mode) {
         HostMode hm;
-        if (!order_mode(nnz, nmodes, dims, idx, mode, inner_sort, threads, hm))
+        if (!order_mode(nnz, nmodes, dims, idx, mode, inner_sort ? lex.p : nullptr, threads, hm))
             return bail(fail(AMPED_ERR_OOM, "host allocation failed in the reorder of mode %d", mode));
         if (mode == 0) {
-            t->xnorm2 = norm2_merged(hm, nmodes, idx, vals, inner_sort ? inner_mode(nmodes, dims, 0) : -1, threads);
+            t->xnorm2 = norm2_merged(hm, nmodes, idx, vals, inner_sort, threads);
             if (t->xnorm2 < 0.0) return bail(fail(AMPED_ERR_OOM, "host allocation failed computing the tensor norm"));
         }
         if (!classify_rows(hm, short_thr, threads) || !cut_segments(hm, items))
@@ -525,7 +575,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
 }
 
 amped_status amped_tensor_destroy(amped_tensor_t t) {
-    g_err.clear();
+    begin_call();
     if (!t) return AMPED_OK;
     cudaDeviceSynchronize();
     delete t;
@@ -533,7 +583,7 @@ amped_status amped_tensor_destroy(amped_tensor_t t) {
 }
 
 amped_status amped_tensor_info(amped_tensor_t t, int64_t* nnz, int* nmodes, int64_t* dims) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (nnz) *nnz = t->nnz;
     if (nmodes) *nmodes = t->N;
@@ -544,7 +594,7 @@ amped_status amped_tensor_info(amped_tensor_t t, int64_t* nnz, int* nmodes, int6
 
 amped_status amped_mttkrp(amped_tensor_t t, int mode, const void* const* factors, amped_dtype fdtype, int R,
                           float* out, void* stream) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (mode < 0 || mode >= t->N) return fail(AMPED_ERR_INVALID, "mode %d outside 0..%d", mode, t->N - 1);
     int vec = 0;
@@ -555,7 +605,7 @@ amped_status amped_mttkrp(amped_tensor_t t, int mode, const void* const* factors
 
 amped_status amped_mttkrp_all(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
                               float* const* outs, void* stream) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (!outs) return fail(AMPED_ERR_INVALID, "output pointer array is NULL");
     int vec = 0;
@@ -573,7 +623,7 @@ amped_status amped_mttkrp_all(amped_tensor_t t, const void* const* factors, ampe
 
 amped_status amped_mttkrp_all_host(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
                                    float* const* outs, void* stream) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (!outs || !factors) return fail(AMPED_ERR_INVALID, "factor or output pointer array is NULL");
     int vec = 0;
@@ -645,7 +695,7 @@ amped_status amped_mttkrp_all_host(amped_tensor_t t, const void* const* factors,
 
 amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R, float* m_out,
                              void* stream) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (!t->coo) return fail(AMPED_ERR_INVALID, "handle was created without caller-order coordinates (keep_coo)");
     int vec = 0;
@@ -677,7 +727,7 @@ amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped
 
 amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
                            const float* gvals, float* const* grads, void* stream) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (!grads) return fail(AMPED_ERR_INVALID, "gradient pointer array is NULL");
     if (t->nnz > 0 && !gvals) return fail(AMPED_ERR_INVALID, "gvals is NULL");
@@ -702,7 +752,7 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
                              int32_t* perm, int32_t* rows_long, int32_t* rowptr_long, int32_t* seg_row,
                              int32_t* seg_nz, int32_t* splits, int32_t* rows_short, int32_t* rowptr_short,
                              int32_t* seg_short) {
-    g_err.clear();
+    begin_call();
     if (nmodes < 1 || nmodes > AMPED_MAX_MODES || !dims || nnz < 0 || nnz > (int64_t)INT32_MAX - 4 * kPad)
         return fail(AMPED_ERR_INVALID, "bad tensor shape");
     if (mode < 0 || mode >= nmodes) return fail(AMPED_ERR_INVALID, "mode %d outside 0..%d", mode, nmodes - 1);
@@ -715,8 +765,11 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
     const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, 0);
     if (bad >= 0) return fail(AMPED_ERR_INDEX, "nonzero %lld has a coordinate outside dims", (long long)bad);
     HostMode hm;
-    if (!order_mode(nnz, nmodes, dims, idx, mode, inner_order != 1, 0, hm) || !classify_rows(hm, thr, 0) ||
-        !cut_segments(hm, items))
+    HostBuf<int32_t> lex;
+    const bool inner_sort = inner_order != 1;
+    if ((inner_sort && !lex_order(nnz, nmodes, dims, idx, 0, lex)) ||
+        !order_mode(nnz, nmodes, dims, idx, mode, inner_sort ? lex.p : nullptr, 0, hm) ||
+        !classify_rows(hm, thr, 0) || !cut_segments(hm, items))
         return fail(AMPED_ERR_OOM, "host allocation failed");
     if (sizes) {
         sizes->nnz = nnz;
@@ -747,7 +800,7 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
 
 amped_status amped_norm2_host(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, const float* vals,
                               int inner_order, double* norm2) {
-    g_err.clear();
+    begin_call();
     if (!norm2) return fail(AMPED_ERR_INVALID, "norm2 is NULL");
     if (nmodes < 1 || nmodes > AMPED_MAX_MODES || !dims || nnz < 0 || nnz > (int64_t)INT32_MAX - 4 * kPad)
         return fail(AMPED_ERR_INVALID, "bad tensor shape");
@@ -758,10 +811,12 @@ amped_status amped_norm2_host(int64_t nnz, int nmodes, const int64_t* dims, cons
     const int64_t bad = find_bad_index(nnz, nmodes, dims, idx, 0);
     if (bad >= 0) return fail(AMPED_ERR_INDEX, "nonzero %lld has a coordinate outside dims", (long long)bad);
     HostMode hm;
+    HostBuf<int32_t> lex;
     const bool inner_sort = inner_order != 1;
-    if (!order_mode(nnz, nmodes, dims, idx, 0, inner_sort, 0, hm))
+    if ((inner_sort && !lex_order(nnz, nmodes, dims, idx, 0, lex)) ||
+        !order_mode(nnz, nmodes, dims, idx, 0, inner_sort ? lex.p : nullptr, 0, hm))
         return fail(AMPED_ERR_OOM, "host allocation failed");
-    const double v = norm2_merged(hm, nmodes, idx, vals, inner_sort ? inner_mode(nmodes, dims, 0) : -1, 0);
+    const double v = norm2_merged(hm, nmodes, idx, vals, inner_sort, 0);
     if (v < 0.0) return fail(AMPED_ERR_OOM, "host allocation failed");
     *norm2 = v;
     return AMPED_OK;
@@ -769,7 +824,7 @@ amped_status amped_norm2_host(int64_t nnz, int nmodes, const int64_t* dims, cons
 
 amped_status amped_cp_completion_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
                                       float* const* grads, double* loss, void* stream) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (!grads) return fail(AMPED_ERR_INVALID, "gradient pointer array is NULL");
     int vec = 0;
@@ -793,7 +848,7 @@ amped_status amped_cp_completion_grad(amped_tensor_t t, const void* const* facto
 }
 
 amped_status amped_tensor_norm2(amped_tensor_t t, double* norm2) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (!norm2) return fail(AMPED_ERR_INVALID, "norm2 is NULL");
     *norm2 = t->xnorm2;
@@ -865,7 +920,7 @@ extern "C" {
 
 amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, double* grams, double* stats,
                                 int flags, void* stream) {
-    g_err.clear();
+    begin_call();
     const void* cf[AMPED_MAX_MODES];
     int vec = 0;
     amped_status s = als_check(t, factors, R, grams, stats, flags, cf, &vec);
@@ -879,7 +934,7 @@ amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, 
 
 amped_status amped_cp_als_update(amped_tensor_t t, int mode, float* const* factors, int R, double* grams,
                                  double* stats, int flags, void* stream) {
-    g_err.clear();
+    begin_call();
     const void* cf[AMPED_MAX_MODES];
     int vec = 0;
     amped_status s = als_check(t, factors, R, grams, stats, flags, cf, &vec);
@@ -892,7 +947,7 @@ amped_status amped_cp_als_update(amped_tensor_t t, int mode, float* const* facto
 
 amped_status amped_cp_als_normalize(amped_tensor_t t, float* const* factors, int R, double* grams, float* lambda,
                                     void* stream) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (!factors || !grams || !lambda) return fail(AMPED_ERR_INVALID, "factors, grams or lambda is NULL");
     if (R < 1 || R > als_max_rank())
@@ -908,7 +963,7 @@ amped_status amped_cp_als_normalize(amped_tensor_t t, float* const* factors, int
 }
 
 amped_status amped_set_kernel_events(amped_tensor_t t, void* start, void* stop) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     t->ev_start = start;
     t->ev_stop = stop;
@@ -918,42 +973,12 @@ amped_status amped_set_kernel_events(amped_tensor_t t, void* start, void* stop) 
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Allocation-free MTTKRP: the same kernels, with their scratch in a fixed
-// static device array instead of the handle's allocations.
+// Allocation-free MTTKRP: the same kernels, with their scratch in the fixed
+// static device array g_noalloc_scratch instead of the handle's allocations.
 // ---------------------------------------------------------------------------
-namespace {
-
-// The scratch array itself.  Host code must not use this name as an address:
-// on the host it is only a stand-in; the device address comes from
-// cudaGetSymbolAddress below, looked up once per device.
-static __device__ __align__(256) unsigned char g_noalloc_scratch[AMPED_NOALLOC_SCRATCH_BYTES];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (first call per device looks it up).
-amped_status noalloc_scratch(void** addr) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return fail(AMPED_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
-        g_noalloc_addr[dev] = ptr;
-    }
-    *addr = g_noalloc_addr[dev];
-    return AMPED_OK;
-}
-
-}  // namespace
-
 extern "C" amped_status amped_mttkrp_noalloc(amped_tensor_t t, int mode, const void* const* factors,
                                              amped_dtype fdtype, int R, float* out, void* stream) {
-    g_err.clear();
+    begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (mode < 0 || mode >= t->N) return fail(AMPED_ERR_INVALID, "mode %d outside 0..%d", mode, t->N - 1);
     int vec = 0;
@@ -973,9 +998,20 @@ extern "C" amped_status amped_mttkrp_noalloc(amped_tensor_t t, int mode, const v
                     "mode %d at rank %d needs %zu bytes of scratch, more than the %u-byte static buffer; "
                     "use amped_mttkrp or a larger segment_items",
                     mode, R, need, (unsigned)AMPED_NOALLOC_SCRATCH_BYTES);
+    int dev = -1;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return cuda_fail(de, "cudaGetDevice");
+    if (dev != t->device)
+        return fail(AMPED_ERR_INVALID, "device %d is current but the handle lives on device %d", dev, t->device);
     void* base = nullptr;
-    s = noalloc_scratch(&base);
-    if (s != AMPED_OK) return s;
+    cudaError_t lookup = cudaErrorInvalidSymbol;
+    if (dev >= 0 && dev < kMaxDevices) {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        base = g_noalloc_addr[dev];
+        lookup = g_noalloc_err[dev];
+    }
+    if (!base && lookup == cudaSuccess) lookup = cudaErrorInvalidSymbol;
+    if (!base) return cuda_fail(lookup, "static scratch of the allocation-free MTTKRP unavailable on this device");
     unsigned char* b = static_cast<unsigned char*>(base);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(b, 0, sizeof(int), st);  // the ticket counter must start at zero
@@ -1004,12 +1040,15 @@ extern "C" amped_status amped_mttkrp_noalloc(amped_tensor_t t, int mode, const v
     p.S = dm.S;
     p.R = R;
     p.nnz = (int32_t)t->nnz;
+    if (t->ev_start) cudaEventRecord(static_cast<cudaEvent_t>(t->ev_start), st);
     int rc;
     switch (fdtype) {
         case AMPED_F32: rc = launch_mttkrp_f32(nin, p, 0, st); break;
         case AMPED_BF16: rc = launch_mttkrp_bf16(nin, p, 0, st); break;
         default: rc = launch_mttkrp_f16(nin, p, 0, st); break;
     }
+    if (t->ev_stop) cudaEventRecord(static_cast<cudaEvent_t>(t->ev_stop), st);
+    t->ev_start = t->ev_stop = nullptr;
     if (rc != 0) return cuda_fail((cudaError_t)rc, "MTTKRP kernel launch");
     ++g_launches;
     CombineParams c{};

@@ -141,21 +141,30 @@ bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
     return true;
 }
 
-int inner_mode(int nmodes, const int64_t* dims, int mode) {
-    int inner = -1;
-    for (int n = 0; n < nmodes; ++n)
-        if (n != mode && (inner < 0 || dims[n] > dims[inner])) inner = n;
-    return inner;
+void mode_priority(int nmodes, const int64_t* dims, int* prio) {
+    for (int n = 0; n < nmodes; ++n) prio[n] = n;
+    std::stable_sort(prio, prio + nmodes, [&](int a, int b) { return dims[a] > dims[b]; });
 }
 
-bool order_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, bool inner_sort,
+bool lex_order(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int threads, HostBuf<int32_t>& out) {
+    int prio[AMPED_MAX_MODES];
+    mode_priority(nmodes, dims, prio);
+    // least significant key first; every pass is stable, so ties keep the earlier passes' order
+    HostMode cur, prev;
+    for (int p = nmodes - 1; p >= 0; --p) {
+        if (!sort_mode(nnz, nmodes, dims, idx, prio[p], threads, cur, p == nmodes - 1 ? nullptr : prev.perm.p))
+            return false;
+        std::swap(cur.perm.p, prev.perm.p);
+        std::swap(cur.perm.n, prev.perm.n);
+    }
+    std::swap(out.p, prev.perm.p);
+    std::swap(out.n, prev.perm.n);
+    return true;
+}
+
+bool order_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int mode, const int32_t* lex,
                 int threads, HostMode& hm) {
-    const int inner = inner_sort ? inner_mode(nmodes, dims, mode) : -1;
-    if (inner < 0) return sort_mode(nnz, nmodes, dims, idx, mode, threads, hm);
-    // lexicographic (i_mode, i_inner): sort by the inner key, then stably by i_mode
-    HostMode pre;
-    return sort_mode(nnz, nmodes, dims, idx, inner, threads, pre) &&
-           sort_mode(nnz, nmodes, dims, idx, mode, threads, hm, pre.perm.p);
+    return sort_mode(nnz, nmodes, dims, idx, mode, threads, hm, lex);
 }
 
 bool classify_rows(HostMode& hm, int threshold, int threads) {
@@ -321,7 +330,8 @@ void caller_column(int64_t nnz, int nmodes, const int32_t* idx, int mode, int32_
     for (int64_t k = 0; k < nnz; ++k) dst[k] = idx[k * nmodes + mode];
 }
 
-double norm2_merged(const HostMode& hm, int nmodes, const int32_t* idx, const float* vals, int inner, int threads) {
+double norm2_merged(const HostMode& hm, int nmodes, const int32_t* idx, const float* vals, bool lex_sorted,
+                    int threads) {
     const int T = nthreads(threads);
     constexpr int64_t kRowsPerChunk = 4096;
     const int64_t nch = (hm.I + kRowsPerChunk - 1) / kRowsPerChunk;
@@ -352,36 +362,37 @@ double norm2_merged(const HostMode& hm, int nmodes, const int32_t* idx, const fl
             double s = 0.0;
             const int64_t i_end = std::min<int64_t>(hm.I, (c + 1) * kRowsPerChunk);
             for (int64_t i = c * kRowsPerChunk; i < i_end; ++i) {
-                int64_t a = hm.rowptr[(size_t)i];
-                const int64_t b = hm.rowptr[(size_t)i + 1];
-                while (a < b) {
-                    int64_t e = b;
-                    if (inner >= 0) {
-                        const int32_t key = idx[(int64_t)hm.perm[(size_t)a] * nmodes + inner];
-                        e = a + 1;
-                        while (e < b && idx[(int64_t)hm.perm[(size_t)e] * nmodes + inner] == key) ++e;
-                    }
-                    if (e - a == 1) {
-                        const double v = vals[hm.perm[(size_t)a]];
+                const int64_t a = hm.rowptr[(size_t)i], b = hm.rowptr[(size_t)i + 1];
+                if (lex_sorted) {  // repeated coordinates are adjacent: sum each run in copy order
+                    for (int64_t j = a; j < b;) {
+                        double v = 0.0;
+                        int64_t q = j;
+                        while (q < b && same(hm.perm[(size_t)q], hm.perm[(size_t)j])) v += vals[hm.perm[(size_t)q++]];
                         s += v * v;
-                    } else {
-                        try {
-                            run.assign(hm.perm.p + a, hm.perm.p + e);
-                        } catch (...) {
-#pragma omp atomic write
-                            failed = true;
-                            break;
-                        }
-                        std::stable_sort(run.begin(), run.end(), less);  // equal coordinates keep copy order
-                        for (size_t j = 0; j < run.size();) {
-                            double v = 0.0;
-                            size_t q = j;
-                            while (q < run.size() && same(run[q], run[j])) v += vals[run[q++]];
-                            s += v * v;
-                            j = q;
-                        }
+                        j = q;
                     }
-                    a = e;
+                    continue;
+                }
+                if (b - a == 1) {
+                    const double v = vals[hm.perm[(size_t)a]];
+                    s += v * v;
+                    continue;
+                }
+                if (b == a) continue;
+                try {
+                    run.assign(hm.perm.p + a, hm.perm.p + b);
+                } catch (...) {
+#pragma omp atomic write
+                    failed = true;
+                    continue;
+                }
+                std::stable_sort(run.begin(), run.end(), less);  // equal coordinates keep copy order
+                for (size_t j = 0; j < run.size();) {
+                    double v = 0.0;
+                    size_t q = j;
+                    while (q < run.size() && same(run[q], run[j])) v += vals[run[q++]];
+                    s += v * v;
+                    j = q;
                 }
             }
             part[(size_t)c] = s;

@@ -102,10 +102,10 @@ def check_plan(dims, idx, mode, items, inner_order="lexicographic", short_rows=0
     keys = idx[:, mode]
     if inner_order == "stable":  # by the mode's coordinate, ties in caller order
         base = np.argsort(keys, kind="stable")
-    else:  # by (mode coordinate, coordinate of the largest other mode), ties in caller order
-        others = [n for n in range(len(dims)) if n != mode]
-        inner = max(others, key=lambda n: (dims[n], -n)) if others else None
-        base = np.lexsort((idx[:, inner], keys)) if inner is not None else np.argsort(keys, kind="stable")
+    else:  # by the mode coordinate, then the other coordinates (largest dimension first, ties by lower
+        # mode index), ties in caller order
+        others = sorted((n for n in range(len(dims)) if n != mode), key=lambda n: (-dims[n], n))
+        base = np.lexsort(tuple([np.arange(nnz)] + [idx[:, n] for n in reversed(others)] + [keys]))
     lens = np.bincount(keys, minlength=I)
     rp = np.concatenate([[0], np.cumsum(lens)])
     thr = 32 if short_rows == 0 else (1 if short_rows < 0 else min(short_rows, 125))
