@@ -4,13 +4,16 @@
 One step = MTTKRP for every mode of the tensor, back to back, with fixed
 input factors (the paper's metric: time to compute MTTKRP along all modes
 in one iteration, Sec. 5.1), output zero rows and split-row combine
-included, preprocessing excluded.  Default workload: the 3-mode power-law
-tensor 10M x 5M x 2M with 200M nonzeros (Zipf(1.1) over a random
-permutation of each mode), rank 32, fp32 factors; the bf16-factor run is
-reported beside it.  Inputs (2.4 GB of streams per mode) exceed the 129 MB
-L2, so no flush is needed between steps.
+included, preprocessing excluded.  Default workload: the billion-scale
+4-mode power-law tensor 50M x 20M x 5M x 1000 with 1.0B nonzeros (modes 0-2
+Zipf(1.2) over a random permutation of each mode, mode 3 uniform, lognormal
+values), rank 32, fp32 factors; the bf16-factor run is reported beside it.
+Inputs (16 GB of streams per mode) exceed the 129 MB L2, so no flush is
+needed between steps.  CPU baselines timed on the host in the same run: the
+single-threaded FP64 oracle and an all-cores OpenMP FP64 MTTKRP, each on a
+bounded sample of the same draw.
 
-    python bench.py [--steps K] [--warmup W] [--workload zipf3] [--impl reference]
+    python bench.py [--steps K] [--warmup W] [--workload zipf4] [--impl reference]
 
 Multi-GPU (torchrun): every rank runs an independent replica on its own
 GPU (no collective on the data path); value = all ranks' nonzeros / the
@@ -44,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="zipf3", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="zipf4", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--scale", type=float, default=1.0, help="scale nnz and dims (debug)")
     ap.add_argument("--segment-items", type=int, default=0)
     ap.add_argument("--inner-order", default="lexicographic", choices=["lexicographic", "stable"])
@@ -216,6 +219,36 @@ def workload_config(w, args):
             "stream_memory": getattr(args, "stream_memory", "device"),
             "l2": "inputs_exceed_l2 (no flush)",
             "parallelism": "single GPU per rank; ranks run independent replicas"}
+
+
+# --------------------------------------------------------------------------- CPU baselines
+def cpu_baselines(c, F, w, m_oracle=12_000_000, m_openmp=50_000_000):
+    """The FP64 oracle on one core and the OpenMP FP64 MTTKRP on every core,
+    each timed over all modes on the first M nonzeros of the seeded draw (the
+    nonzeros are drawn i.i.d., so a prefix is a random sample): about 10-20 s
+    of work each on the GPU machine's host."""
+    import cpu_baseline
+    import oracle
+    M = min(m_oracle, c.nnz)
+    ci, cv = np.ascontiguousarray(c.idx[:M]), np.ascontiguousarray(c.vals[:M])
+    t1 = time.perf_counter()
+    for m in range(c.nmodes):
+        oracle.mttkrp(c.dims, ci, cv, F, m)
+    cpu_s = time.perf_counter() - t1
+    out = {"value": M / cpu_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"first {M} nonzeros of {w.name}, all {c.nmodes} modes, FP64 single thread ({cpu_s:.1f} s)"}
+    Mo = min(m_openmp, c.nnz)
+    ci, cv = np.ascontiguousarray(c.idx[:Mo]), np.ascontiguousarray(c.vals[:Mo])
+    orders = [cpu_baseline.order(c.dims, ci, m) for m in range(c.nmodes)]  # preprocessing, not timed
+    t1 = time.perf_counter()
+    for m in range(c.nmodes):
+        cpu_baseline.mttkrp(c.dims, ci, cv, F, m, orders[m])
+    omp_s = time.perf_counter() - t1
+    out["openmp"] = {"value": Mo / omp_s / 1e9, "unit": UNIT, "cores": cpu_baseline.threads(), "kind": "openmp",
+                     "sample": f"first {Mo} nonzeros of {w.name}, all {c.nmodes} modes, FP64 on "
+                               f"{cpu_baseline.threads()} threads over rows ordered by the output coordinate "
+                               f"(the ordering is not timed; {omp_s:.1f} s)"}
+    return out
 
 
 # --------------------------------------------------------------------------- reference arm (FP64 CPU oracle)
@@ -403,17 +436,7 @@ def run_ours(args, w, world, rank, local, pg):
     del Fd
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        M = min(12_000_000, c.nnz)  # about 10-20 s of single-thread FP64 work
-        ci = np.ascontiguousarray(c.idx[:M])
-        cv = np.ascontiguousarray(c.vals[:M])
-        t1 = time.perf_counter()
-        for m in range(c.nmodes):
-            oracle.mttkrp(c.dims, ci, cv, F, m)
-        cpu_s = time.perf_counter() - t1
-        line["cpu_baseline"] = {"value": M / cpu_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {M} nonzeros of {w.name}, all {c.nmodes} modes, FP64 single "
-                                          f"thread ({cpu_s:.1f} s)"}
+        line["cpu_baseline"] = cpu_baselines(c, F, w)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -18,6 +18,9 @@ LIB = os.path.join(HERE, "libamped.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp", "-I" + os.path.join(HERE, "..", "include")]
+# extra nvcc flags (e.g. -D definitions of the kernels' compile-time constants); part of the
+# object files' staleness key so a change rebuilds
+EXTRA = os.environ.get("AMPED_NVCC_FLAGS", "").split()
 
 
 def _sources():
@@ -36,11 +39,21 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _flags_file():
+    """A file whose content is the extra flags; rewritten only when they change."""
+    path = os.path.join(BUILD, "extra_flags.txt")
+    text = " ".join(EXTRA)
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
+    return path
+
+
 def _compile(src, verbose=False):
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    if not _stale(obj, [src] + _headers()):
+    if not _stale(obj, [src, os.path.join(BUILD, "extra_flags.txt")] + _headers()):
         return obj
-    cmd = [NVCC] + ARCH + COMMON + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [NVCC] + ARCH + COMMON + EXTRA + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -56,6 +69,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     if force:
         for f in glob.glob(os.path.join(BUILD, "*.o")):
             os.remove(f)
+    _flags_file()
     with cf.ThreadPoolExecutor(max_workers=jobs or min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if force or _stale(LIB, objs):
