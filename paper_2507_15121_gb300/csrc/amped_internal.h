@@ -108,6 +108,11 @@ bool cut_segments(HostMode& hm, int items);
 //   dst[k] = idx[perm[k]][src_mode]   and   dst[k] = vals[perm[k]]
 void gather_column(const HostMode& hm, int nmodes, const int32_t* idx, int src_mode, int32_t* dst, int threads);
 void gather_values(const HostMode& hm, const float* vals, float* dst, int threads);
+// Every input slot's column and the values of a mode-ordered copy in one pass
+// over the nonzeros (one visit of each nonzero's coordinate record):
+// cols[s][k] = idx[perm[k]][slot_mode[s]], dvals[k] = vals[perm[k]].
+void gather_copy(const HostMode& hm, int nmodes, const int32_t* idx, const float* vals, int nin, const int* slot_mode,
+                 int32_t* const* cols, float* dvals, int threads);
 // Caller-order column: dst[k] = idx[k][mode].
 void caller_column(int64_t nnz, int nmodes, const int32_t* idx, int mode, int32_t* dst, int threads);
 

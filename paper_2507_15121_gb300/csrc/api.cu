@@ -492,9 +492,10 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         delete t;
         return s;
     };
-    HostBuf<int32_t> col;
+    HostBuf<int32_t> col;  // [N-1][stride]: the input slots' columns of one copy
     HostBuf<float> fcol;
-    if (!col.alloc(stride) || !fcol.alloc(stride)) return bail(fail(AMPED_ERR_OOM, "host allocation failed"));
+    if (!col.alloc(stride * (size_t)std::max(1, nmodes - 1)) || !fcol.alloc(stride))
+        return bail(fail(AMPED_ERR_OOM, "host allocation failed"));
     cudaError_t e;
     HostBuf<int32_t> lex;  // lexicographic order of all coordinates; every mode's copy is a stable sort of it
     if (inner_sort && !lex_order(nnz, nmodes, dims, idx, threads, lex))
@@ -523,20 +524,20 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
             (e = upload(t, &dm.rows_S, hm.rows_S.p, (size_t)hm.Sr, (size_t)hm.Sr + kPad)) != cudaSuccess ||
             (e = upload(t, &dm.seg_short, hm.seg_short.p, (size_t)hm.S_S + 1, (size_t)hm.S_S + 1)) != cudaSuccess)
             return bail(cuda_fail(e, "device copy of the row tables"));
-        if (nmodes > 1) {
-            if ((e = t->salloc(reinterpret_cast<void**>(&dm.idx), (size_t)(nmodes - 1) * stride * 4)) != cudaSuccess)
-                return bail(cuda_fail(e, "copy of the coordinates"));
-            const int nin = input_slots(nmodes, dims, mode, inner_sort, dm.slot_mode);
-            for (int slot = 0; slot < nin; ++slot) {
-                gather_column(hm, nmodes, idx, dm.slot_mode[slot], col.p, threads);
-                std::memset(col.p + nnz, 0, (stride - (size_t)nnz) * 4);
-                if ((e = cudaMemcpy(dm.idx + (size_t)slot * stride, col.p, stride * 4, cudaMemcpyDefault)) !=
-                    cudaSuccess)
-                    return bail(cuda_fail(e, "copy of the coordinates"));
-            }
+        const int nin = nmodes > 1 ? input_slots(nmodes, dims, mode, inner_sort, dm.slot_mode) : 0;
+        {
+            int32_t* cols[AMPED_MAX_MODES];
+            for (int slot = 0; slot < nin; ++slot) cols[slot] = col.p + (size_t)slot * stride;
+            gather_copy(hm, nmodes, idx, vals, nin, dm.slot_mode, cols, fcol.p, threads);
+            for (int slot = 0; slot < nin; ++slot) std::memset(cols[slot] + nnz, 0, (stride - (size_t)nnz) * 4);
+            std::memset(fcol.p + nnz, 0, (stride - (size_t)nnz) * 4);
         }
-        gather_values(hm, vals, fcol.p, threads);
-        std::memset(fcol.p + nnz, 0, (stride - (size_t)nnz) * 4);
+        if (nin > 0) {
+            if ((e = t->salloc(reinterpret_cast<void**>(&dm.idx), (size_t)nin * stride * 4)) != cudaSuccess)
+                return bail(cuda_fail(e, "copy of the coordinates"));
+            if ((e = cudaMemcpy(dm.idx, col.p, (size_t)nin * stride * 4, cudaMemcpyDefault)) != cudaSuccess)
+                return bail(cuda_fail(e, "copy of the coordinates"));
+        }
         if ((e = upload_stream(t, &dm.val, fcol.p, stride, stride)) != cudaSuccess)
             return bail(cuda_fail(e, "copy of the values"));
         if (keep_perm && (e = upload_stream(t, &dm.perm, hm.perm.p, (size_t)nnz, stride)) != cudaSuccess)

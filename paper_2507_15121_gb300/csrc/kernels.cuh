@@ -459,6 +459,102 @@ __device__ __forceinline__ void stage_batch(WarpStage<NIN>& st, int lane, const 
     }
 }
 
+// Factored path (the fiber factorisation of compressed-sparse-fiber MTTKRP,
+// done per lane group) for a staged batch of kBatch nonzeros that lies inside
+// one row and inside the segment.  Group g walks the RUN = kBatch/G
+// consecutive nonzeros g*RUN .. g*RUN+RUN-1.  The copy orders a row
+// lexicographically by the input slots, so along the walk slot 0 changes
+// least often, then slot 1, and so on: a "run" at level l is a stretch of
+// nonzeros with equal slots 0..l.  The product of a nonzero factors as
+//   val * A_0(c0) * ... * A_{L-1}(c_{L-1}) * A_L(c_L)      (L = NIN - 1)
+// so the row sum is, per level-0 run, A_0 times the sum over its level-1
+// runs of A_1 times ... times the sum of val * A_L over the level-(L-1) run.
+// t[l] holds the open level-l run's inner sum; when slot l changes, the run
+// closes (t[l-1] += x[l] * t[l], or acc for l = 0) and the new run's row x[l]
+// is gathered.  That row is needed only when its run closes, so its latency
+// is hidden behind the run, while the innermost slot's rows (needed by every
+// nonzero) are gathered ZA nonzeros ahead.  Rows delivered to the lanes per
+// nonzero: one for slot L plus one per run start of the outer slots, instead
+// of NIN; on power-law tensors that is 1.5-2 instead of 3 at four modes.
+template <typename T, int VEC, int LPN, int NIN, int ZA>
+__device__ __forceinline__ void fiber_batch(const WarpStage<NIN>& st, int g, const T* const (&fl)[NIN], uint32_t R,
+                                            float (&acc)[VEC]) {
+    static_assert(std::is_same<T, float>::value && VEC == 8, "fp32 rows of 8 ranks per lane");
+    constexpr int G = 32 / LPN, RUN = kBatch / G, L = NIN - 1;
+    static_assert(L >= 1 && RUN % ZA == 0, "factored path shape");
+    Raw<T, VEC> x[L];  // the open run's row, per level
+    unsigned long long t[L][VEC / 2];  // open run's inner sums, as fp32 pairs
+    int cur[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        cur[l] = -1;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) x[l].w[e] = 0u;
+#pragma unroll
+        for (int e = 0; e < VEC / 2; ++e) t[l][e] = 0ull;
+    }
+    auto close_into = [&](const Raw<T, VEC>& xr, unsigned long long (&tt)[VEC / 2], unsigned long long* dst) {
+#pragma unroll
+        for (int e = 0; e < VEC / 2; ++e) {
+            dst[e] = fma2(pk(__uint_as_float(xr.w[2 * e]), __uint_as_float(xr.w[2 * e + 1])), tt[e], dst[e]);
+            tt[e] = 0ull;
+        }
+    };
+    unsigned long long a2[VEC / 2];  // acc as pairs while the batch runs
+#pragma unroll
+    for (int e = 0; e < VEC / 2; ++e) a2[e] = pk(acc[2 * e], acc[2 * e + 1]);
+    const int j0 = g * RUN;
+#pragma unroll 1
+    for (int u = 0; u < RUN; u += ZA) {
+        Rec<NIN> r[ZA];
+        Raw<T, VEC> z[ZA];
+#pragma unroll
+        for (int a = 0; a < ZA; ++a) {
+            r[a] = st.get(j0 + u + a);
+            z[a].load(fl[L] + (uint64_t)(uint32_t)r[a].idx(L) * R);
+        }
+#pragma unroll
+        for (int a = 0; a < ZA; ++a) {
+            bool ch[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l) ch[l] = (l > 0 && ch[l - 1]) || r[a].idx(l) != cur[l];
+            // close the runs that end here, innermost first
+#pragma unroll
+            for (int l = L - 1; l >= 1; --l)
+                if (ch[l]) close_into(x[l], t[l], t[l - 1]);
+            if (ch[0]) close_into(x[0], t[0], a2);
+            // open the new runs
+#pragma unroll
+            for (int l = 0; l < L; ++l)
+                if (ch[l]) {
+                    cur[l] = r[a].idx(l);
+                    x[l].load(fl[l] + (uint64_t)(uint32_t)cur[l] * R);
+                }
+            const unsigned long long vv = pk(r[a].val(), r[a].val());
+#pragma unroll
+            for (int e = 0; e < VEC / 2; ++e)
+                t[L - 1][e] = fma2(vv, pk(__uint_as_float(z[a].w[2 * e]), __uint_as_float(z[a].w[2 * e + 1])), t[L - 1][e]);
+        }
+    }
+#pragma unroll
+    for (int l = L - 1; l >= 1; --l) close_into(x[l], t[l], t[l - 1]);
+    close_into(x[0], t[0], a2);
+#pragma unroll
+    for (int e = 0; e < VEC / 2; ++e) upk(a2[e], acc[2 * e], acc[2 * e + 1]);
+}
+
+// Shapes that take the factored path (fp32 rows of 8 ranks per lane, 3- and
+// 4-mode tensors: register room for the open runs at 64 registers) and how
+// many nonzeros ahead the innermost rows are gathered.  On GB300 it is 9-12 %
+// faster than the chunk path on the 4-mode power-law tensor and equal on the
+// 3-mode one; deeper look-ahead and L1 prefetch of the next rows measured no
+// better or slower.
+template <typename T, int VEC, int NIN>
+struct Factored {
+    static constexpr bool value = std::is_same<T, float>::value && VEC == 8 && (NIN == 2 || NIN == 3);
+    static constexpr int ahead = NIN == 2 ? 2 : 1;
+};
+
 // One warp processes one segment.  The warp holds G = 32/LPN groups; at
 // step u of a chunk, group g takes nonzero base + u*G + g, so all control
 // flow (batches, chunks, row ends) is uniform across the warp.  A chunk that
@@ -563,6 +659,12 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
             __syncwarp();
         }
         if (kb + kBatch < nz_e) prefetch_batch<NIN>(p, kb + kBatch, lane);  // next batch into L2
+        if constexpr (!RES && Factored<T, VEC, NIN>::value) {
+            if (kb >= nz_s && kb + kBatch <= nz_e && kb + kBatch <= rend) {  // the batch lies inside row i
+                if (active) fiber_batch<T, VEC, LPN, NIN, Factored<T, VEC, NIN>::ahead>(st, g, fl, R, acc);
+                continue;
+            }
+        }
 #pragma unroll 1
         for (int c0 = 0; c0 < kBatch; c0 += CHN) {
             const int base = kb + c0;

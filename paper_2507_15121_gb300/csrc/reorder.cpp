@@ -76,23 +76,25 @@ bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
     if (!hm.perm.alloc((size_t)nnz) || !hm.rowptr.alloc((size_t)I + 1)) return false;
     const int T = nthreads(threads);
 
+    // the sequence being sorted (caller indices 0..nnz-1, or `order` when given) and its
+    // keys, gathered once so that every later pass reads them contiguously
+    HostBuf<int32_t> key, tkey, tmp;
+    if (!key.alloc((size_t)nnz) || !tkey.alloc((size_t)nnz) || !tmp.alloc((size_t)nnz)) return false;
+#pragma omp parallel for schedule(static) num_threads(T)
+    for (int64_t j = 0; j < nnz; ++j) key[(size_t)j] = idx[(order ? (int64_t)order[j] : j) * nmodes + mode];
+
     // level 1: bucket by the high bits of the key, at most 2^16 buckets
     int bits = 0;
     while ((int64_t(1) << bits) < I) ++bits;
     const int shift = bits > 16 ? bits - 16 : 0;
     const int64_t B = ((I - 1) >> shift) + 1;
     std::vector<int64_t> hist((size_t)T * (size_t)B, 0);
-    HostBuf<int32_t> tmp;
-    if (!tmp.alloc((size_t)nnz)) return false;
-    // the sequence being sorted: caller indices 0..nnz-1, or `order` when given
-    auto elem = [&](int64_t j) -> int32_t { return order ? order[j] : (int32_t)j; };
-    auto key = [&](int64_t k) -> int64_t { return idx[k * nmodes + mode]; };
 #pragma omp parallel num_threads(T)
     {
         const int t = omp_get_thread_num();
         const int64_t lo = nnz * t / T, hi = nnz * (t + 1) / T;
         int64_t* h = hist.data() + (size_t)t * B;
-        for (int64_t j = lo; j < hi; ++j) ++h[key(elem(j)) >> shift];
+        for (int64_t j = lo; j < hi; ++j) ++h[key[(size_t)j] >> shift];
     }
     // exclusive scan in (bucket, thread) order keeps the scatter stable
     std::vector<int64_t> bstart((size_t)B + 1);
@@ -112,8 +114,10 @@ bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
         const int64_t lo = nnz * t / T, hi = nnz * (t + 1) / T;
         int64_t* off = hist.data() + (size_t)t * B;
         for (int64_t j = lo; j < hi; ++j) {
-            const int32_t k = elem(j);
-            tmp[(size_t)off[key(k) >> shift]++] = k;
+            const int32_t kv = key[(size_t)j];
+            const int64_t dst = off[kv >> shift]++;
+            tmp[(size_t)dst] = order ? order[j] : (int32_t)j;
+            tkey[(size_t)dst] = kv;
         }
     }
     // level 2: stable counting sort of each bucket by the low bits; fills rowptr
@@ -126,15 +130,13 @@ bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
             const int64_t k0 = bstart[b], k1 = bstart[b + 1];
             const int64_t key0 = b << shift, nkeys = std::min(span, I - key0);
             std::fill(cnt.begin(), cnt.begin() + nkeys + 1, 0);
-            for (int64_t j = k0; j < k1; ++j) ++cnt[(size_t)(key(tmp[j]) - key0) + 1];
+            for (int64_t j = k0; j < k1; ++j) ++cnt[(size_t)(tkey[(size_t)j] - key0) + 1];
             for (int64_t x = 0; x < nkeys; ++x) {
                 cnt[(size_t)x + 1] += cnt[(size_t)x];
                 hm.rowptr[(size_t)(key0 + x)] = (int32_t)(k0 + cnt[(size_t)x]);
             }
-            for (int64_t j = k0; j < k1; ++j) {
-                const int32_t c = tmp[j];
-                hm.perm[(size_t)(k0 + cnt[(size_t)(key(c) - key0)]++)] = c;
-            }
+            for (int64_t j = k0; j < k1; ++j)
+                hm.perm[(size_t)(k0 + cnt[(size_t)(tkey[(size_t)j] - key0)]++)] = tmp[(size_t)j];
         }
     }
     hm.rowptr[(size_t)I] = (int32_t)nnz;
@@ -316,6 +318,18 @@ void gather_column(const HostMode& hm, int nmodes, const int32_t* idx, int src_m
     const int T = nthreads(threads);
 #pragma omp parallel for schedule(static) num_threads(T)
     for (int64_t k = 0; k < hm.nnz; ++k) dst[k] = idx[(int64_t)hm.perm[(size_t)k] * nmodes + src_mode];
+}
+
+void gather_copy(const HostMode& hm, int nmodes, const int32_t* idx, const float* vals, int nin, const int* slot_mode,
+                 int32_t* const* cols, float* dvals, int threads) {
+    const int T = nthreads(threads);
+#pragma omp parallel for schedule(static) num_threads(T)
+    for (int64_t k = 0; k < hm.nnz; ++k) {
+        const int64_t src = hm.perm[(size_t)k];
+        const int32_t* rec = idx + src * nmodes;
+        for (int s = 0; s < nin; ++s) cols[s][k] = rec[slot_mode[s]];
+        dvals[k] = vals[src];
+    }
 }
 
 void gather_values(const HostMode& hm, const float* vals, float* dst, int threads) {
