@@ -29,6 +29,7 @@ import statistics
 import subprocess
 import sys
 import time
+import types
 
 import numpy as np
 
@@ -150,6 +151,18 @@ class ClockSampler:
         self.result = {"sm_mhz": statistics.median(r[0] for r in self.rows),
                        "sm_max_mhz": max(r[1] for r in self.rows), "samples": len(self.rows),
                        "reasons": reasons}
+
+
+def host_waves(w, world: int) -> int:
+    """How many replicas may generate and reorder their tensors at the same time."""
+    if world <= 1:
+        return 1
+    try:
+        avail = next(int(l.split()[1]) * 1024 for l in open("/proc/meminfo") if l.startswith("MemAvailable"))
+    except Exception:
+        return 1
+    need = 80 * max(1, w.nnz)
+    return max(1, min(world, int(0.7 * avail // need)))
 
 
 def distinct_rows(c):
@@ -345,15 +358,24 @@ def run_ours(args, w, world, rank, local, pg):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     K, W = args.steps, args.warmup
-    t0 = time.time()
-    c = synth.make(w)
-    F = synth.factors(c.dims, w.rank, w.seed)
-    U = distinct_rows(c)
-    gen_s = time.time() - t0
-    t0 = time.time()
-    t = amped.Tensor(c.dims, c.idx, c.vals, segment_items=args.segment_items, inner_order=args.inner_order,
-                     short_rows=args.short_rows, stream_memory=args.stream_memory)
-    create_s = time.time() - t0
+    # Replicas build their handles in waves sized to the host memory (a 1B-nonzero tensor
+    # needs about 80 bytes per nonzero on the host while it is generated and reordered);
+    # ranks other than 0 drop their host COO arrays once their handle exists.
+    wave = host_waves(w, world)
+    for r0 in range(0, world, wave):
+        if r0 <= rank < r0 + wave:
+            t0 = time.time()
+            c = synth.make(w)
+            F = synth.factors(c.dims, w.rank, w.seed)
+            U = distinct_rows(c)
+            gen_s = time.time() - t0
+            t0 = time.time()
+            t = amped.Tensor(c.dims, c.idx, c.vals, segment_items=args.segment_items, inner_order=args.inner_order,
+                             short_rows=args.short_rows, stream_memory=args.stream_memory)
+            create_s = time.time() - t0
+            if rank != 0:  # only the shape is used from here on
+                c = types.SimpleNamespace(dims=c.dims, nnz=c.nnz, nmodes=c.nmodes)
+        barrier(pg, device)
     stream = torch.cuda.current_stream()
     Fd = [torch.from_numpy(f).to(device) for f in F]
     peak, peak_kind = peaks()

@@ -675,7 +675,14 @@ int launch_als_apply(const AlsParams& p, const float* M, int64_t rows, float* A,
     const int R = p.R;
     cudaError_t e = cudaMemsetAsync(p.ga, 0, sizeof(double) * ((size_t)R * R + R), st);  // ga, then ip
     if (e != cudaSuccess) return (int)e;
-    if (rows > 0) {
+    if (rows > 0 && als_apply_tc_supported(R)) {
+        // A = M W and ip on the tensor cores, then the Gram of the stored A (when the solve
+        // failed the product does nothing and finish_kernel ignores the Gram)
+        e = (cudaError_t)launch_als_apply_tc(p, M, rows, A, stream, launched);
+        if (e != cudaSuccess) return (int)e;
+        e = (cudaError_t)launch_gram(A, rows, R, p.ga, stream, launched);
+        if (e != cudaSuccess) return (int)e;
+    } else if (rows > 0) {
 #define AMPED_APPLY_CASE(RP)                                                                                    \
     case RP: {                                                                                                 \
         const size_t bytes = ApplyShape<RP>::smem_bytes();                                                     \

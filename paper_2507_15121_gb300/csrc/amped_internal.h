@@ -185,6 +185,10 @@ int launch_als_solve(const AlsParams& p, void* stream, int* launched);
 // A = M W with its Gram and ip unless the solve failed, then the commit of the
 // Gram and, after the last mode, the fit.
 int launch_als_apply(const AlsParams& p, const float* M, int64_t rows, float* A, void* stream, int* launched);
+// The tensor-core apply (als_tc.cu, tcgen05 3xTF32): the ranks it is built for,
+// and its launch (same contract as launch_als_apply without the finish).
+bool als_apply_tc_supported(int R);
+int launch_als_apply_tc(const AlsParams& p, const float* M, int64_t rows, float* A, void* stream, int* launched);
 // Unit-norm columns for every factor, lambda = product of the norms, Grams rescaled.
 int launch_als_normalize(float* const* factors, const int64_t* dims, int N, int R, double* grams, float* lambda,
                          void* stream, int* launched);
