@@ -554,3 +554,42 @@ def test_planted3_full_size_fused_completion_gradient():
         refs = [f.result() for f in futs]
     for m in range(3):
         assert oracle.row_error(got[m], refs[m], floor_frac=1e-6) <= GRAD_BAR, m
+
+
+@pytest.mark.parametrize("nmodes", [3, 4])
+@pytest.mark.parametrize("runs", ["long", "short", "duplicates"])
+@pytest.mark.parametrize("items", [0, 300])
+def test_factored_path_run_structures(nmodes, runs, items):
+    """Rows long enough for whole 128-nonzero batches (the factored path: outer slots gathered
+    at run starts, innermost per nonzero) with controlled runs of the leading coordinates: long
+    runs (few distinct leading values), runs of length one (every nonzero starts new runs), and
+    repeated full coordinates; rows end inside batches and, with 300-item segments, rows span
+    segments.  fp32 against the oracle."""
+    rng = np.random.default_rng(31 + nmodes)
+    dims = (40, 300, 200, 150)[:nmodes]
+    rows = [3, 17, 29]  # three long output rows of mode 0, plus scattered short rows
+    lens = [2000, 777, 131]
+    parts = []
+    for r, n in zip(rows, lens):
+        c = np.zeros((n, nmodes), np.int32)
+        c[:, 0] = r
+        for m in range(1, nmodes):
+            if runs == "long":
+                c[:, m] = rng.integers(0, 4, n)
+            elif runs == "short":
+                c[:, m] = rng.permutation(np.arange(n) % dims[m])
+            else:
+                c[:, m] = rng.integers(0, 3, n)
+        parts.append(c)
+    short = np.stack([rng.integers(0, d, 500) for d in dims], axis=1).astype(np.int32)
+    idx = np.concatenate(parts + [short])
+    idx = idx[rng.permutation(len(idx))]
+    vals = rng.uniform(0, 1, len(idx)).astype(np.float32)
+    F = [rng.uniform(0, 1, (d, 32)).astype(np.float32) for d in dims]
+    t = amped.Tensor(dims, idx, vals, segment_items=items)
+    outs = t.mttkrp_all([dev(f) for f in F])
+    torch.cuda.synchronize()
+    for m in range(nmodes):
+        ref = oracle.mttkrp(dims, idx, vals, F, m)
+        assert oracle.row_error(outs[m].cpu().numpy(), ref) <= FP32_BAR, (m, runs)
+    t.close()
