@@ -661,7 +661,9 @@ amped_status amped_mttkrp_all_host(amped_tensor_t t, const void* const* factors,
         dout[n] = t->stage_out[n];
     }
     // Copies overlap the kernels: the factors mode 0 needs go first, factor 0 is uploaded
-    // while mode 0 runs, and each output is downloaded while the next mode runs.
+    // while mode 0 runs, and the outputs are downloaded while the later modes run.  The
+    // downloads start once the uploads are done, so they do not share the host link with the
+    // upload of factor 0, which every mode after the first waits for.
     if ((e = ensure_copy_streams(t)) != cudaSuccess) return cuda_fail(e, "copy streams");
     cudaStream_t up = static_cast<cudaStream_t>(t->up_stream), down = static_cast<cudaStream_t>(t->down_stream);
     cudaEvent_t* ev = reinterpret_cast<cudaEvent_t*>(t->copy_ev);  // [0] entry, [1] rest in, [2] factor 0 in,
@@ -675,7 +677,8 @@ amped_status amped_mttkrp_all_host(amped_tensor_t t, const void* const* factors,
     for (int n = 1; n < t->N; ++n)
         if ((e = upload(n)) != cudaSuccess) return cuda_fail(e, "factor upload");
     if ((e = cudaEventRecord(ev[1], up)) != cudaSuccess || (e = upload(0)) != cudaSuccess ||
-        (e = cudaEventRecord(ev[2], up)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ev[1], 0)) != cudaSuccess)
+        (e = cudaEventRecord(ev[2], up)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ev[1], 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(down, ev[2], 0)) != cudaSuccess)
         return cuda_fail(e, "factor upload");
     for (int n = 0; n < t->N; ++n) {
         if (n == 1 && (e = cudaStreamWaitEvent(st, ev[2], 0)) != cudaSuccess) return cuda_fail(e, "copy ordering");
