@@ -198,7 +198,9 @@ amped_status amped_norm2_host(int64_t nnz, int nmodes, const int64_t* dims, cons
  * seeing the factors updated before it:
  *   M        = MTTKRP_d(X; A_n, n != d)                         (amped_mttkrp, fp32)
  *   V        = Hadamard product over n != d of grams[n]         (fp64)
- *   A_d      = M V^-1                                           (fp64 Cholesky of V; fp32 apply)
+ *   A_d      = M V^-1                                           (fp64 Cholesky of V; the product
+ *                                                                in fp32, on the tensor cores
+ *                                                                with a 3-term TF32 split at R = 32)
  *   grams[d] = A_d^T A_d of the stored fp32 values              (fp64)
  * The columns are NOT normalised between modes: least-squares updates are covariant under column
  * scaling, so the models [[A_0, ..., A_{N-1}]] equal those of the per-step normalised algorithm.
