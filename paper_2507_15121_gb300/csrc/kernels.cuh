@@ -2,22 +2,25 @@
 //
 // MTTKRP (paper Sec. 3 elementwise computation, Alg. 2), restated for one
 // GB300:
-//  * A "worker" is LPN consecutive lanes of a warp; lane q of a worker owns
+//  * A "lane group" is LPN consecutive lanes of a warp; lane q of a group owns
 //    ranks q*VEC .. q*VEC+VEC-1 of every factor row, so one factor row is one
-//    coalesced LPN*VEC-element access (Alg. 2 gives one thread per rank of a
-//    nonzero; here VEC ranks per thread for 128-bit accesses).
-//  * Workers pull segments from a device-wide ticket counter (the single-GPU
+//    coalesced 256-bit load per lane (Alg. 2 gives one thread per rank of a
+//    nonzero; here 8 fp32 or 16 16-bit ranks per lane).
+//  * Warps pull segments from a device-wide ticket counter (the single-GPU
 //    form of the paper's idle-SM-takes-the-next-partition assignment,
 //    Sec. 4.2) inside a persistent grid.
 //  * A segment is a merge-path slice of the mode-ordered copy (rows +
-//    nonzeros <= items).  The worker streams the segment's coordinate and
-//    value arrays with 128-bit loads (4 nonzeros per lane, L2 evict-first),
-//    broadcasts each nonzero inside the worker with one shuffle per array,
-//    gathers the N-1 input factor rows, and accumulates the row in registers
-//    while the output index is unchanged.  A completed row is stored once;
-//    only rows that straddle a segment boundary leave a partial in the split
-//    buffer, combined afterwards in a fixed order in fp64 (no atomics, so the
-//    result does not depend on scheduling).
+//    nonzeros <= items).  The warp streams the segment's coordinate and value
+//    arrays with 128-bit evict-first loads and stages them as one record per
+//    nonzero in shared memory.  A staged batch that lies inside one row takes
+//    the factored path (fiber_batch: each group walks 16 consecutive nonzeros
+//    and gathers the outer slots' rows only at run starts); other chunks take
+//    the interleaved chunk path (group g takes every G-th nonzero).  The row
+//    is accumulated in registers while the output index is unchanged and
+//    stored once; only rows that straddle a segment boundary leave a partial
+//    in the split buffer, combined afterwards in a fixed order in fp64 (no
+//    atomics, so the result does not depend on scheduling).
+//  * Rows with few nonzeros go to short segments (one row per lane group).
 #pragma once
 
 #include <cuda_bf16.h>
