@@ -198,9 +198,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
-    """DRAM bytes per launch of the MTTKRP kernel from the committed ncu summary,
-    used only while the kernel sources still hash to the captured version."""
+def recorded_traffic(workload: str, dtype: str = "f32"):
+    """DRAM bytes per launch of the MTTKRP kernel (fp32 or bf16 factors) from the
+    committed ncu summary, used only while the kernel sources still hash to the
+    captured version."""
     path = os.path.join(ROOT, "profiles", f"mttkrp_{workload}_traffic.txt")
     try:
         kv = {}
@@ -210,7 +211,7 @@ def recorded_traffic(workload: str):
                 kv[k.strip()] = v.strip()
         if kv.get("kernel_source_sha") != kernel_source_hash():
             return None
-        return float(kv["dram_bytes_per_launch_f32"])
+        return float(kv[f"dram_bytes_per_launch_{dtype}"])
     except Exception:
         return None
 
@@ -421,7 +422,9 @@ def run_ours(args, w, world, rank, local, pg):
             "value": world * c.nnz * K / (tot_l * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": tot_l / K,
             "gpu_launches": launches_l,
             "roofline": {"bound": "hbm", "achieved": ach_l, "peak": peak, "unit": "GB/s", "frac": ach_l / peak,
-                         "traffic": None, "kernel": kernel_name("__nv_bfloat16" if name == "bf16" else "__half",
+                         "traffic": (recorded_traffic(w.name, name) if w.rank == 32 and args.scale == 1.0
+                                     else None),
+                         "kernel": kernel_name("__nv_bfloat16" if name == "bf16" else "__half",
                                                                 w.rank, c.nmodes),
                          "algorithmic_bytes_per_mode": Bl, "kernel_ms_per_mode": kl}}
 
