@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--workload", default="zipf4", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--scale", type=float, default=1.0, help="scale nnz and dims (debug)")
     ap.add_argument("--segment-items", type=int, default=0)
-    ap.add_argument("--inner-order", default="lexicographic", choices=["lexicographic", "stable"])
+    ap.add_argument("--inner-order", default="lexicographic",
+                    choices=["lexicographic", "lexicographic_ascending", "stable"])
     ap.add_argument("--short-rows", type=int, default=0, help="short-row threshold (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

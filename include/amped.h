@@ -67,7 +67,9 @@ typedef struct {
     int32_t inner_order;   /* order of the nonzeros inside an output row: 1 = caller order (stable);
                               2 = lexicographic in the other coordinates, the mode with the largest
                               dimension most significant (ties: lower mode index), so consecutive
-                              nonzeros share factor rows the kernel keeps in registers; 0 = default (2) */
+                              nonzeros share factor rows the kernel keeps in registers; 3 = the same
+                              with the smallest dimension most significant; 0 = default (2); other
+                              values are AMPED_ERR_INVALID */
     int32_t short_rows;    /* rows with fewer nonzeros than this (at most 125) are "short": they are
                               sorted by length and processed one row per lane group; longer rows are
                               processed by whole warps along the merge path.  0 = default (32);

@@ -77,12 +77,14 @@ bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
                HostMode& hm, const int32_t* order = nullptr);
 
 // Priority of the coordinates in the inner order: modes by decreasing
-// dimension, ties by increasing mode index (prio[0] is the most significant).
-void mode_priority(int nmodes, const int64_t* dims, int* prio);
+// dimension (by increasing dimension when `ascending`), ties by increasing mode
+// index (prio[0] is the most significant).
+void mode_priority(int nmodes, const int64_t* dims, int* prio, bool ascending = false);
 // Caller indices in lexicographic order of all N coordinates, most significant
 // (highest priority) first; ties keep caller order.  One stable counting sort
 // per mode, least significant first.  Returns false on allocation failure.
-bool lex_order(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int threads, HostBuf<int32_t>& out);
+bool lex_order(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int threads, HostBuf<int32_t>& out,
+               bool ascending = false);
 // Mode order: by i_mode; inside a row in the order of `lex` (the lexicographic
 // order from lex_order, which orders a row by the other coordinates in priority
 // order), or in caller order when lex is null.  Stable.

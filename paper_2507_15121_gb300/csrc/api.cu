@@ -136,10 +136,10 @@ struct DevMode {
 // modes in priority order (decreasing dimension), which is the order the copy
 // sorts a row by, so slot 0 changes least often along a row and the kernel's
 // cached factor rows are reused longest.  Otherwise: increasing mode index.
-int input_slots(int nmodes, const int64_t* dims, int mode, bool inner_sort, int* slot_mode) {
+int input_slots(int nmodes, const int64_t* dims, int mode, bool inner_sort, bool ascending, int* slot_mode) {
     int prio[AMPED_MAX_MODES];
     if (inner_sort) {
-        mode_priority(nmodes, dims, prio);
+        mode_priority(nmodes, dims, prio, ascending);
     } else {
         for (int n = 0; n < nmodes; ++n) prio[n] = n;
     }
@@ -453,7 +453,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
             return fail(AMPED_ERR_INVALID, "dims[%d]=%lld outside 1..2^31-%d", n, (long long)dims[n], 4 * kPad);
     if (nnz > 0 && (!idx || !vals)) return fail(AMPED_ERR_INVALID, "idx or vals is NULL");
     int items = 0, threads = 0, max_rank = 64, short_thr = 32;
-    bool keep_perm = true, keep_coo = true, inner_sort = true, host_streams = false;
+    bool keep_perm = true, keep_coo = true, inner_sort = true, ascending = false, host_streams = false;
     if (opts) {
         if (opts->segment_items < 0 || opts->max_rank < 0 || opts->host_threads < 0)
             return fail(AMPED_ERR_INVALID, "negative option");
@@ -462,7 +462,10 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         threads = opts->host_threads;
         keep_perm = opts->keep_perm != 2;
         keep_coo = opts->keep_coo != 2;
+        if (opts->inner_order < 0 || opts->inner_order > 3)
+            return fail(AMPED_ERR_INVALID, "inner_order=%d is not 0, 1, 2 or 3", opts->inner_order);
         inner_sort = opts->inner_order != 1;
+        ascending = opts->inner_order == 3;
         if (opts->short_rows > 0) short_thr = std::min(opts->short_rows, kShortNnz + 1);
         if (opts->short_rows < 0) short_thr = 1;  // every non-empty row takes the long path
         if (opts->stream_memory < 0 || opts->stream_memory > 2)
@@ -498,7 +501,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         return bail(fail(AMPED_ERR_OOM, "host allocation failed"));
     cudaError_t e;
     HostBuf<int32_t> lex;  // lexicographic order of all coordinates; every mode's copy is a stable sort of it
-    if (inner_sort && !lex_order(nnz, nmodes, dims, idx, threads, lex))
+    if (inner_sort && !lex_order(nnz, nmodes, dims, idx, threads, lex, ascending))
         return bail(fail(AMPED_ERR_OOM, "host allocation failed in the lexicographic order"));
     for (int mode = 0; mode < nmodes; ++mode) {
         HostMode hm;
@@ -524,7 +527,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
             (e = upload(t, &dm.rows_S, hm.rows_S.p, (size_t)hm.Sr, (size_t)hm.Sr + kPad)) != cudaSuccess ||
             (e = upload(t, &dm.seg_short, hm.seg_short.p, (size_t)hm.S_S + 1, (size_t)hm.S_S + 1)) != cudaSuccess)
             return bail(cuda_fail(e, "device copy of the row tables"));
-        const int nin = nmodes > 1 ? input_slots(nmodes, dims, mode, inner_sort, dm.slot_mode) : 0;
+        const int nin = nmodes > 1 ? input_slots(nmodes, dims, mode, inner_sort, ascending, dm.slot_mode) : 0;
         {
             int32_t* cols[AMPED_MAX_MODES];
             for (int slot = 0; slot < nin; ++slot) cols[slot] = col.p + (size_t)slot * stride;
@@ -770,8 +773,9 @@ amped_status amped_plan_mode(int64_t nnz, int nmodes, const int64_t* dims, const
     if (bad >= 0) return fail(AMPED_ERR_INDEX, "nonzero %lld has a coordinate outside dims", (long long)bad);
     HostMode hm;
     HostBuf<int32_t> lex;
+    if (inner_order < 0 || inner_order > 3) return fail(AMPED_ERR_INVALID, "inner_order=%d is not 0..3", inner_order);
     const bool inner_sort = inner_order != 1;
-    if ((inner_sort && !lex_order(nnz, nmodes, dims, idx, 0, lex)) ||
+    if ((inner_sort && !lex_order(nnz, nmodes, dims, idx, 0, lex, inner_order == 3)) ||
         !order_mode(nnz, nmodes, dims, idx, mode, inner_sort ? lex.p : nullptr, 0, hm) ||
         !classify_rows(hm, thr, 0) || !cut_segments(hm, items))
         return fail(AMPED_ERR_OOM, "host allocation failed");
@@ -816,8 +820,9 @@ amped_status amped_norm2_host(int64_t nnz, int nmodes, const int64_t* dims, cons
     if (bad >= 0) return fail(AMPED_ERR_INDEX, "nonzero %lld has a coordinate outside dims", (long long)bad);
     HostMode hm;
     HostBuf<int32_t> lex;
+    if (inner_order < 0 || inner_order > 3) return fail(AMPED_ERR_INVALID, "inner_order=%d is not 0..3", inner_order);
     const bool inner_sort = inner_order != 1;
-    if ((inner_sort && !lex_order(nnz, nmodes, dims, idx, 0, lex)) ||
+    if ((inner_sort && !lex_order(nnz, nmodes, dims, idx, 0, lex, inner_order == 3)) ||
         !order_mode(nnz, nmodes, dims, idx, 0, inner_sort ? lex.p : nullptr, 0, hm))
         return fail(AMPED_ERR_OOM, "host allocation failed");
     const double v = norm2_merged(hm, nmodes, idx, vals, inner_sort, 0);

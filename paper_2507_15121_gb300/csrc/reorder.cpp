@@ -143,14 +143,18 @@ bool sort_mode(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx,
     return true;
 }
 
-void mode_priority(int nmodes, const int64_t* dims, int* prio) {
+void mode_priority(int nmodes, const int64_t* dims, int* prio, bool ascending) {
     for (int n = 0; n < nmodes; ++n) prio[n] = n;
-    std::stable_sort(prio, prio + nmodes, [&](int a, int b) { return dims[a] > dims[b]; });
+    if (ascending)
+        std::stable_sort(prio, prio + nmodes, [&](int a, int b) { return dims[a] < dims[b]; });
+    else
+        std::stable_sort(prio, prio + nmodes, [&](int a, int b) { return dims[a] > dims[b]; });
 }
 
-bool lex_order(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int threads, HostBuf<int32_t>& out) {
+bool lex_order(int64_t nnz, int nmodes, const int64_t* dims, const int32_t* idx, int threads, HostBuf<int32_t>& out,
+               bool ascending) {
     int prio[AMPED_MAX_MODES];
-    mode_priority(nmodes, dims, prio);
+    mode_priority(nmodes, dims, prio, ascending);
     // least significant key first; every pass is stable, so ties keep the earlier passes' order
     HostMode cur, prev;
     for (int p = nmodes - 1; p >= 0; --p) {

@@ -16,6 +16,13 @@ try:
 except ImportError:  # the planning query works without torch
     torch = None
 
+# amped_opts.inner_order codes: the order of the nonzeros inside an output row
+INNER_ORDERS = {
+    "stable": 1,                     # caller order
+    "lexicographic": 2,              # other coordinates, largest dimension most significant
+    "lexicographic_ascending": 3,    # other coordinates, smallest dimension most significant
+}
+
 
 def _dtype_code(t) -> int:
     if t.dtype == torch.float32:
@@ -55,12 +62,12 @@ class Tensor:
             raise ValueError("idx must be [nnz, N] and vals [nnz]")
         self.nnz = int(idx.shape[0])
         dims_a = np.asarray(self.dims, dtype=np.int64)
-        if inner_order not in ("lexicographic", "stable"):
-            raise ValueError("inner_order must be 'lexicographic' or 'stable'")
+        if inner_order not in INNER_ORDERS:
+            raise ValueError(f"inner_order must be one of {sorted(INNER_ORDERS)}")
         if stream_memory not in ("device", "host"):
             raise ValueError("stream_memory must be 'device' or 'host'")
         opts = _lib.Opts(segment_items, 1 if keep_perm else 2, 1 if keep_coo else 2, max_rank, host_threads,
-                         2 if inner_order == "lexicographic" else 1, short_rows, 2 if stream_memory == "host" else 1)
+                         INNER_ORDERS[inner_order], short_rows, 2 if stream_memory == "host" else 1)
         h = ctypes.c_void_p()
         _lib.check(L.amped_tensor_create(self.nnz, len(self.dims), dims_a.ctypes.data,
                                          idx.ctypes.data if self.nnz else None,
@@ -276,7 +283,7 @@ def plan_mode(dims, idx, mode: int, segment_items: int = 0, inner_order: str = "
     dims_a = np.asarray(dims, dtype=np.int64)
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     nnz = int(idx.shape[0])
-    io = 2 if inner_order == "lexicographic" else 1
+    io = INNER_ORDERS[inner_order]
     args = (nnz, len(dims_a), dims_a.ctypes.data, idx.ctypes.data if nnz else None, mode, segment_items, io,
             short_rows)
     sz = _lib.PlanSizes()

@@ -91,6 +91,17 @@ def test_argument_errors_without_gpu(L):
     assert L.amped_tensor_create(2, 2, dims_a.ctypes.data, idx.ctypes.data, vals.ctypes.data, ctypes.byref(opts),
                                  ctypes.byref(h)) == _lib.ERR_INVALID
     assert b"stream_memory" in L.amped_last_error()
+    # inner_order must be 0..3 (create and the host-only planning queries)
+    opts = _lib.Opts(0, 0, 0, 0, 0, 4, 0, 0)
+    assert L.amped_tensor_create(2, 2, dims_a.ctypes.data, idx.ctypes.data, vals.ctypes.data, ctypes.byref(opts),
+                                 ctypes.byref(h)) == _lib.ERR_INVALID
+    assert b"inner_order" in L.amped_last_error()
+    sz = _lib.PlanSizes()
+    assert L.amped_plan_mode(2, 2, dims_a.ctypes.data, idx.ctypes.data, 0, 0, -1, 0, ctypes.byref(sz),
+                             *([None] * 9)) == _lib.ERR_INVALID
+    n2 = ctypes.c_double()
+    assert L.amped_norm2_host(2, 2, dims_a.ctypes.data, idx.ctypes.data, vals.ctypes.data, 5,
+                              ctypes.byref(n2)) == _lib.ERR_INVALID
     # calls on a NULL handle fail cleanly
     assert L.amped_mttkrp(None, 0, None, 0, 32, None, None) == _lib.ERR_INVALID
     assert L.amped_tensor_destroy(None) == _lib.OK
@@ -102,9 +113,10 @@ def check_plan(dims, idx, mode, items, inner_order="lexicographic", short_rows=0
     keys = idx[:, mode]
     if inner_order == "stable":  # by the mode's coordinate, ties in caller order
         base = np.argsort(keys, kind="stable")
-    else:  # by the mode coordinate, then the other coordinates (largest dimension first, ties by lower
-        # mode index), ties in caller order
-        others = sorted((n for n in range(len(dims)) if n != mode), key=lambda n: (-dims[n], n))
+    else:  # by the mode coordinate, then the other coordinates (largest dimension first, or smallest
+        # first for the ascending order; ties by lower mode index), ties in caller order
+        sign = 1 if inner_order == "lexicographic_ascending" else -1
+        others = sorted((n for n in range(len(dims)) if n != mode), key=lambda n: (sign * dims[n], n))
         base = np.lexsort(tuple([np.arange(nnz)] + [idx[:, n] for n in reversed(others)] + [keys]))
     lens = np.bincount(keys, minlength=I)
     rp = np.concatenate([[0], np.cumsum(lens)])
@@ -240,7 +252,8 @@ def make_case(name, dims, nnz, seed):
 @pytest.mark.parametrize("name,dims,nnz,seed", CASES)
 @pytest.mark.parametrize("items", [1, 7, 32, 1024, 10 ** 6])
 @pytest.mark.parametrize("inner_order,short_rows", [("lexicographic", 0), ("stable", 0), ("lexicographic", -1),
-                                                    ("stable", 5), ("lexicographic", 200)])
+                                                    ("stable", 5), ("lexicographic", 200),
+                                                    ("lexicographic_ascending", 0)])
 def test_plan_and_simulated_kernel_match_oracle(name, dims, nnz, seed, items, inner_order, short_rows):
     idx, vals = make_case(name, dims, nnz, seed)
     F = [np.random.default_rng(seed + n).uniform(0, 1, (d, 3)).astype(np.float32) for n, d in enumerate(dims)]
@@ -269,7 +282,7 @@ def _norm2_host(L, dims, idx, vals, inner_order):
 
 
 @pytest.mark.parametrize("dims", [(30, 20, 10), (12, 9, 8, 5), (40, 30), (6, 5, 4, 3, 3, 2)])
-@pytest.mark.parametrize("inner_order", [0, 1, 2])
+@pytest.mark.parametrize("inner_order", [0, 1, 2, 3])
 def test_tensor_norm_sums_repeated_coordinates(L, dims, inner_order):
     """The host norm ||X||^2 with repeated coordinates summed (the ALS fit's ||X||) equals the
     oracle's, for every inner order, with many repeats (some rows hold most of the nonzeros)."""
