@@ -559,12 +559,15 @@ def test_planted3_full_size_fused_completion_gradient():
 @pytest.mark.parametrize("nmodes", [3, 4])
 @pytest.mark.parametrize("runs", ["long", "short", "duplicates"])
 @pytest.mark.parametrize("items", [0, 300])
-def test_factored_path_run_structures(nmodes, runs, items):
+@pytest.mark.parametrize("dt,R", [(torch.float32, 32), (torch.bfloat16, 32), (torch.float16, 32),
+                                  (torch.bfloat16, 64)])
+def test_factored_path_run_structures(nmodes, runs, items, dt, R):
     """Rows long enough for whole 128-nonzero batches (the factored path: outer slots gathered
     at run starts, innermost per nonzero) with controlled runs of the leading coordinates: long
     runs (few distinct leading values), runs of length one (every nonzero starts new runs), and
     repeated full coordinates; rows end inside batches and, with 300-item segments, rows span
-    segments.  fp32 against the oracle."""
+    segments.  fp32 factors against the oracle; 16-bit factors (16 ranks per lane: 16 lane
+    groups at R = 32, 8 at R = 64) against the oracle on the same rounded factors."""
     rng = np.random.default_rng(31 + nmodes)
     dims = (40, 300, 200, 150)[:nmodes]
     rows = [3, 17, 29]  # three long output rows of mode 0, plus scattered short rows
@@ -585,11 +588,16 @@ def test_factored_path_run_structures(nmodes, runs, items):
     idx = np.concatenate(parts + [short])
     idx = idx[rng.permutation(len(idx))]
     vals = rng.uniform(0, 1, len(idx)).astype(np.float32)
-    F = [rng.uniform(0, 1, (d, 32)).astype(np.float32) for d in dims]
+    F = [rng.uniform(0, 1, (d, R)).astype(np.float32) for d in dims]
     t = amped.Tensor(dims, idx, vals, segment_items=items)
-    outs = t.mttkrp_all([dev(f) for f in F])
+    Fd = [dev(f, dt) for f in F]
+    outs = t.mttkrp_all(Fd)
     torch.cuda.synchronize()
+    if dt == torch.float32:
+        Fo, kind = F, "f32"
+    else:
+        Fo, kind = [host_bits(f) for f in Fd], ("bf16" if dt == torch.bfloat16 else "f16")
     for m in range(nmodes):
-        ref = oracle.mttkrp(dims, idx, vals, F, m)
-        assert oracle.row_error(outs[m].cpu().numpy(), ref) <= FP32_BAR, (m, runs)
+        ref = oracle.mttkrp(dims, idx, vals, Fo, m, kind)
+        assert oracle.row_error(outs[m].cpu().numpy(), ref) <= FP32_BAR, (m, runs, kind)
     t.close()
