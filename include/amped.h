@@ -44,7 +44,9 @@ extern "C" {
 typedef enum {
     AMPED_OK = 0,
     AMPED_ERR_INVALID = -1,     /* bad argument (null pointer, size, mode, alignment) */
-    AMPED_ERR_INDEX = -2,       /* a coordinate lies outside its mode's range */
+    AMPED_ERR_INDEX = -2,       /* a coordinate lies outside its mode's range (in a build compiled
+                                   with -DAMPED_CHECKS=1 also: a kernel's device bounds check failed;
+                                   the access was clamped and the message names the check) */
     AMPED_ERR_OOM = -3,         /* host or device allocation failed */
     AMPED_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed */
     AMPED_ERR_UNSUPPORTED = -5, /* rank / dtype / mode count this build has no kernel for */

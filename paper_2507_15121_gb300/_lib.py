@@ -10,7 +10,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libamped.so")
+# AMPED_LIB selects another build of the same library (the bounds-checked one,
+# for example); it must exist like the default one.
+LIB_PATH = os.environ.get("AMPED_LIB") or os.path.join(_HERE, "libamped.so")
 
 OK, ERR_INVALID, ERR_INDEX, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 F32, BF16, F16 = 0, 1, 2

@@ -39,21 +39,21 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _flags_file():
+def _flags_file(build_dir, flags):
     """A file whose content is the extra flags; rewritten only when they change."""
-    path = os.path.join(BUILD, "extra_flags.txt")
-    text = " ".join(EXTRA)
+    path = os.path.join(build_dir, "extra_flags.txt")
+    text = " ".join(flags)
     if not os.path.exists(path) or open(path).read() != text:
         with open(path, "w") as f:
             f.write(text)
     return path
 
 
-def _compile(src, verbose=False):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    if not _stale(obj, [src, os.path.join(BUILD, "extra_flags.txt")] + _headers()):
+def _compile(src, build_dir, flags, verbose=False):
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
+    if not _stale(obj, [src, os.path.join(build_dir, "extra_flags.txt")] + _headers()):
         return obj
-    cmd = [NVCC] + ARCH + COMMON + EXTRA + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [NVCC] + ARCH + COMMON + flags + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -63,23 +63,30 @@ def _compile(src, verbose=False):
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, flags: list | None = None,
+          lib_path: str | None = None, build_dir: str | None = None) -> str:
+    """Compile and link the library.  `flags` (default: AMPED_NVCC_FLAGS) are
+    extra nvcc flags, e.g. ["-DAMPED_CHECKS=1"] for the bounds-checked build;
+    `lib_path` / `build_dir` place a variant build outside the package."""
+    flags = EXTRA if flags is None else list(flags)
+    lib = lib_path or LIB
+    bdir = build_dir or BUILD
+    os.makedirs(bdir, exist_ok=True)
     srcs = _sources()
     if force:
-        for f in glob.glob(os.path.join(BUILD, "*.o")):
+        for f in glob.glob(os.path.join(bdir, "*.o")):
             os.remove(f)
-    _flags_file()
+    _flags_file(bdir, flags)
     with cf.ThreadPoolExecutor(max_workers=jobs or min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, bdir, flags, verbose), srcs))
+    if force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fopenmp", "-lgomp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -8,9 +8,27 @@
 
 #include "../../include/amped.h"
 
+// Checked builds (nvcc -DAMPED_CHECKS=1): the MTTKRP and sampled-model kernels
+// check every gather coordinate, output row id, stream position and row-table
+// window against its array, record the first failed check in the handle's
+// device error word and clamp the access in bounds; the entry point then waits
+// for the stream and returns AMPED_ERR_INDEX.  Off (0) in the default build.
+#ifndef AMPED_CHECKS
+#define AMPED_CHECKS 0
+#endif
+
 namespace amped {
 
 constexpr int kMaxIn = AMPED_MAX_MODES - 1;  // input modes of one MTTKRP
+
+// Failed-check codes in err[0] (err[1] = the offending index, err[2] = slot or mode).
+enum CheckCode : int32_t {
+    kCheckCoord = 1,    // gather coordinate outside its factor's rows
+    kCheckOutRow = 2,   // output row id outside the output mode's rows
+    kCheckStream = 3,   // stream position beyond the copy's arrays
+    kCheckRowptr = 4,   // row-table window beyond the long rows' table
+    kCheckShort = 5,    // short segment wider than one staged batch
+};
 constexpr int kPad = 256;                    // elements of slack after every stream array
 constexpr int kCombineSlots = 32;            // partial slots summed by one combine task
 
@@ -149,6 +167,11 @@ struct MttkrpParams {
     double* loss;                // residual mode: accumulates 1/2 sum (m - x)^2 (may be null)
     int32_t I, S, R, nnz;        // I: long rows; S: long segments
     int32_t S_S;                 // short segments (tickets S .. S+S_S-1)
+    // used by checked builds only (AMPED_CHECKS)
+    int32_t* err;                // [4] first failed check {code, index, slot, 0}
+    int32_t fdim[kMaxIn];        // rows of each input slot's factor
+    int32_t out_rows;            // rows of the output mode
+    int64_t stride;              // elements per stream array
 };
 
 struct CombineParams {
@@ -166,6 +189,10 @@ struct SampleParams {
     const void* fac[AMPED_MAX_MODES];
     float* m;                             // [nnz] (+ slack for the vector store)
     int32_t nnz, R, nmodes;
+    // used by checked builds only (AMPED_CHECKS)
+    int32_t* err;                         // [4] first failed check
+    int32_t fdim[AMPED_MAX_MODES];        // rows of each factor
+    int64_t stride;                       // elements per coordinate array
 };
 
 // One CP-ALS mode update (als.cu).

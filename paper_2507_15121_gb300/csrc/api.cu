@@ -2,6 +2,7 @@
 // checking, scratch management and kernel dispatch.  Host code only; the
 // kernels live in kernels.cuh (instantiated per dtype) and combine.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <omp.h>
 
 #include <algorithm>
@@ -60,6 +61,23 @@ amped_status cuda_fail(cudaError_t e, const char* what) {
     return fail(e == cudaErrorMemoryAllocation ? AMPED_ERR_OOM : AMPED_ERR_CUDA, "%s: %s", what,
                 cudaGetErrorString(e));
 }
+
+// NVTX range over a host-side phase (the reorder, the uploads, each mode's
+// launches), shown by Nsight Systems and Nsight Compute; without an attached
+// tool the push and pop do nothing.
+struct Range {
+    explicit Range(const char* fmt, ...) {
+        char buf[96];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        nvtxRangePushA(buf);
+    }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 // Host-side fault injection for testing clean-up paths: AMPED_FAULT=alloc:K
 // makes the K-th device allocation (1-based) inside each entry-point call
@@ -162,6 +180,7 @@ struct amped_tensor {
     float* part = nullptr;   // [maxS][2][rcap]
     double* tsum = nullptr;  // [maxTask][rcap]
     int* queue = nullptr;
+    int32_t* err = nullptr;  // checked builds: the kernels' failed-check word [4]
     int32_t maxS = 0, maxTask = 0, rcap = 0;
     void* ev_start = nullptr;
     void* ev_stop = nullptr;
@@ -354,11 +373,44 @@ amped_status check_call(amped_tensor* t, const void* const* factors, amped_dtype
 }
 
 // One mode: reset the ticket counter, run the persistent kernel, combine split rows.
+// Checked builds: waits for the stream and reports (then clears) the first
+// bounds check the kernels failed since the last look.  Default builds: no-op.
+amped_status check_device(amped_tensor* t, cudaStream_t st, const char* what) {
+#if AMPED_CHECKS
+    if (!t->err) return AMPED_OK;
+    int32_t w[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(w, t->err, sizeof w, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (w[0] != 0) {
+        static const char* names[] = {"?", "gather coordinate", "output row id", "stream position", "row-table window",
+                                      "short segment width"};
+        cudaMemset(t->err, 0, sizeof w);
+        return fail(AMPED_ERR_INDEX, "%s: device bounds check failed: %s %d (slot %d)", what,
+                    names[(w[0] > 0 && w[0] <= kCheckShort) ? w[0] : 0], w[1], w[2]);
+    }
+#else
+    (void)t;
+    (void)st;
+    (void)what;
+#endif
+    return AMPED_OK;
+}
+
+// The fields of MttkrpParams that checked builds use.
+void set_bounds(const amped_tensor* t, const DevMode& dm, MttkrpParams& p) {
+    p.err = t->err;
+    for (int slot = 0; slot < t->N - 1; ++slot) p.fdim[slot] = (int32_t)t->dims[dm.slot_mode[slot]];
+    p.out_rows = (int32_t)dm.I;
+    p.stride = t->stride;
+}
+
 amped_status run_mode(amped_tensor* t, int mode, const void* const* factors, amped_dtype fdtype, int R, int vec,
                       float* out, const float* gval, cudaStream_t st, bool residual = false, double* loss = nullptr) {
     const DevMode& dm = t->m[mode];
     if (!out) return fail(AMPED_ERR_INVALID, "output for mode %d is NULL", mode);
     if (!aligned(out, vec > 1 ? 16 : 4)) return fail(AMPED_ERR_INVALID, "output for mode %d is misaligned", mode);
+    Range range("amped mttkrp mode %d%s", mode, residual ? " (residual)" : (gval ? " (gradient)" : ""));
     amped_status s = ensure_scratch(t, R);
     if (s != AMPED_OK) return s;
     if (t->N == 1) {  // no input modes: the product is empty, out(i,r) = sum of the row's values
@@ -392,6 +444,7 @@ amped_status run_mode(amped_tensor* t, int mode, const void* const* factors, amp
     p.nnz = (int32_t)t->nnz;
     p.fout = residual ? factors[mode] : nullptr;
     p.loss = residual ? loss : nullptr;
+    set_bounds(t, dm, p);
     if (t->ev_start) cudaEventRecord(static_cast<cudaEvent_t>(t->ev_start), st);
     int rc;
     if (residual) {
@@ -425,14 +478,14 @@ amped_status run_mode(amped_tensor* t, int mode, const void* const* factors, amp
     rc = launch_combine(c, st, &launched);
     g_launches += launched;
     if (rc != 0) return cuda_fail((cudaError_t)rc, "split-row combine launch");
-    return AMPED_OK;
+    return check_device(t, st, "MTTKRP kernel");
 }
 
 }  // namespace
 
 extern "C" {
 
-const char* amped_version(void) { return "amped-gb300 0.1 (sm_103a)"; }
+const char* amped_version(void) { return AMPED_CHECKS ? "amped-gb300 0.1 (sm_103a, checked)" : "amped-gb300 0.1 (sm_103a)"; }
 
 const char* amped_last_error(void) { return g_err.c_str(); }
 
@@ -479,6 +532,7 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         return fail(AMPED_ERR_INDEX, "nonzero %lld has coordinate (%s) outside dims", (long long)bad, c.c_str());
     }
 
+    Range range("amped_tensor_create (%lld nonzeros, %d modes)", (long long)nnz, nmodes);
     amped_tensor* t = new (std::nothrow) amped_tensor;
     if (!t) return fail(AMPED_ERR_OOM, "host allocation failed");
     cudaGetDevice(&t->device);
@@ -501,9 +555,13 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
         return bail(fail(AMPED_ERR_OOM, "host allocation failed"));
     cudaError_t e;
     HostBuf<int32_t> lex;  // lexicographic order of all coordinates; every mode's copy is a stable sort of it
-    if (inner_sort && !lex_order(nnz, nmodes, dims, idx, threads, lex, ascending))
-        return bail(fail(AMPED_ERR_OOM, "host allocation failed in the lexicographic order"));
+    {
+        Range lex_range("lexicographic order");
+        if (inner_sort && !lex_order(nnz, nmodes, dims, idx, threads, lex, ascending))
+            return bail(fail(AMPED_ERR_OOM, "host allocation failed in the lexicographic order"));
+    }
     for (int mode = 0; mode < nmodes; ++mode) {
+        Range mode_range("mode %d copy: reorder, plan, upload", mode);
         HostMode hm;
         if (!order_mode(nnz, nmodes, dims, idx, mode, inner_sort ? lex.p : nullptr, threads, hm))
             return bail(fail(AMPED_ERR_OOM, "host allocation failed in the reorder of mode %d", mode));
@@ -534,6 +592,16 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
             gather_copy(hm, nmodes, idx, vals, nin, dm.slot_mode, cols, fcol.p, threads);
             for (int slot = 0; slot < nin; ++slot) std::memset(cols[slot] + nnz, 0, (stride - (size_t)nnz) * 4);
             std::memset(fcol.p + nnz, 0, (stride - (size_t)nnz) * 4);
+#if AMPED_CHECKS
+            // Checked builds only: AMPED_FAULT=coord:K corrupts the slot-0 coordinate of copy
+            // position K of mode 0 after validation, so a test can watch a kernel's bounds check
+            // catch it (the access is clamped; the call reports AMPED_ERR_INDEX).
+            if (mode == 0 && nin > 0 && nnz > 0) {
+                const char* f = std::getenv("AMPED_FAULT");
+                if (f && std::strncmp(f, "coord:", 6) == 0)
+                    cols[0][(size_t)(std::atoll(f + 6) % nnz)] = (int32_t)dims[dm.slot_mode[0]] + 3;
+            }
+#endif
         }
         if (nin > 0) {
             if ((e = t->salloc(reinterpret_cast<void**>(&dm.idx), (size_t)nin * stride * 4)) != cudaSuccess)
@@ -573,6 +641,11 @@ amped_status amped_tensor_create(int64_t nnz, int nmodes, const int64_t* dims, c
     }
     amped_status s = ensure_scratch(t, max_rank);
     if (s != AMPED_OK) return bail(s);
+#if AMPED_CHECKS
+    if ((e = t->dalloc(reinterpret_cast<void**>(&t->err), 4 * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMemset(t->err, 0, 4 * sizeof(int32_t))) != cudaSuccess)
+        return bail(cuda_fail(e, "error word of the bounds checks"));
+#endif
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(cuda_fail(e, "tensor create"));
     *out = t;
     return AMPED_OK;
@@ -630,6 +703,7 @@ amped_status amped_mttkrp_all_host(amped_tensor_t t, const void* const* factors,
     begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (!outs || !factors) return fail(AMPED_ERR_INVALID, "factor or output pointer array is NULL");
+    Range range("amped mttkrp_all_host");
     int vec = 0;
     // host pointers: check everything except device alignment, which the staging provides
     const void* dummy[AMPED_MAX_MODES];
@@ -721,6 +795,10 @@ amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped
     p.nnz = (int32_t)t->nnz;
     p.R = R;
     p.nmodes = t->N;
+    p.err = t->err;
+    for (int n = 0; n < t->N; ++n) p.fdim[n] = (int32_t)t->dims[n];
+    p.stride = t->stride;
+    Range range("amped cp_sample");
     int rc;
     switch (fdtype) {
         case AMPED_F32: rc = launch_sample_f32(p, stream); break;
@@ -729,7 +807,7 @@ amped_status amped_cp_sample(amped_tensor_t t, const void* const* factors, amped
     }
     if (rc != 0) return cuda_fail((cudaError_t)rc, "sampled-model kernel launch");
     ++g_launches;
-    return AMPED_OK;
+    return check_device(t, static_cast<cudaStream_t>(stream), "sampled-model kernel");
 }
 
 amped_status amped_cp_grad(amped_tensor_t t, const void* const* factors, amped_dtype fdtype, int R,
@@ -836,6 +914,7 @@ amped_status amped_cp_completion_grad(amped_tensor_t t, const void* const* facto
     begin_call();
     if (!t) return fail(AMPED_ERR_INVALID, "tensor handle is NULL");
     if (!grads) return fail(AMPED_ERR_INVALID, "gradient pointer array is NULL");
+    Range range("amped cp_completion_grad");
     int vec = 0;
     amped_status s = check_call(t, factors, fdtype, R, -1, &vec);
     if (s != AMPED_OK) return s;
@@ -935,6 +1014,7 @@ amped_status amped_cp_als_sweep(amped_tensor_t t, float* const* factors, int R, 
     amped_status s = als_check(t, factors, R, grams, stats, flags, cf, &vec);
     if (s != AMPED_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Range range("amped cp_als_sweep (rank %d)", R);
     if ((s = als_begin(t, factors, R, grams, stats, flags, st)) != AMPED_OK) return s;
     for (int m = 0; m < t->N; ++m)
         if ((s = als_mode(t, m, factors, cf, R, vec, grams, stats, m == t->N - 1, st)) != AMPED_OK) return s;
@@ -1049,6 +1129,7 @@ extern "C" amped_status amped_mttkrp_noalloc(amped_tensor_t t, int mode, const v
     p.S = dm.S;
     p.R = R;
     p.nnz = (int32_t)t->nnz;
+    set_bounds(t, dm, p);
     if (t->ev_start) cudaEventRecord(static_cast<cudaEvent_t>(t->ev_start), st);
     int rc;
     switch (fdtype) {
@@ -1074,5 +1155,5 @@ extern "C" amped_status amped_mttkrp_noalloc(amped_tensor_t t, int mode, const v
     rc = launch_combine(c, st, &launched);
     g_launches += launched;
     if (rc != 0) return cuda_fail((cudaError_t)rc, "split-row combine launch");
-    return AMPED_OK;
+    return check_device(t, st, "MTTKRP kernel");
 }

@@ -34,6 +34,34 @@
 
 namespace amped {
 
+// ------------------------------------------------------------------ checked builds
+// With AMPED_CHECKS an index outside its array records the first failure in
+// the error word ({code, index, slot}) and is replaced by an in-bounds one (0);
+// without it these helpers are the plain index and the bound is never read.
+__device__ __forceinline__ void check_fail(int32_t* err, int32_t code, int64_t index, int32_t slot) {
+    if (atomicCAS(err, 0, code) == 0) {
+        err[1] = (int32_t)index;
+        err[2] = slot;
+    }
+}
+__device__ __forceinline__ int checked_index(int32_t* err, int32_t code, int c, int bound, int slot) {
+#if AMPED_CHECKS
+    if ((uint32_t)c >= (uint32_t)bound) {
+        check_fail(err, code, c, slot);
+        return 0;
+    }
+#endif
+    return c;
+}
+// coordinate c of input slot n, as a factor row index
+__device__ __forceinline__ uint64_t frow(const MttkrpParams& p, int n, int c) {
+    return (uint64_t)(uint32_t)checked_index(p.err, kCheckCoord, c, p.fdim[n], n);
+}
+// an output row id read from the row tables
+__device__ __forceinline__ int out_row(const MttkrpParams& p, int id) {
+    return checked_index(p.err, kCheckOutRow, id, p.out_rows, -1);
+}
+
 // ------------------------------------------------------------------ loads
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;
@@ -378,6 +406,7 @@ struct StreamBatch {
 template <int NIN>
 __device__ __forceinline__ void load_batch(const MttkrpParams& p, int kl, StreamBatch<NIN>& b) {
     const uint64_t pol = policy_evict_first();
+    kl = checked_index(p.err, kCheckStream, kl, (int)(p.stride - 3), -1);
 #pragma unroll
     for (int n = 0; n < NIN; ++n) b.idx[n] = ld_stream_i4(p.idx[n] + kl, pol);
     if (p.perm == nullptr) {
@@ -480,8 +509,8 @@ __device__ __forceinline__ void stage_batch(WarpStage<NIN>& st, int lane, const 
 // nonzero: one for slot L plus one per run start of the outer slots, instead
 // of NIN; on power-law tensors that is 1.5-2 instead of 3 at four modes.
 template <typename T, int VEC, int LPN, int NIN, int ZA>
-__device__ __forceinline__ void fiber_batch(const WarpStage<NIN>& st, int g, const T* const (&fl)[NIN], uint32_t R,
-                                            float (&acc)[VEC]) {
+__device__ __forceinline__ void fiber_batch(const MttkrpParams& p, const WarpStage<NIN>& st, int g,
+                                            const T* const (&fl)[NIN], uint32_t R, float (&acc)[VEC]) {
     static_assert(std::is_same<T, float>::value && VEC == 8, "fp32 rows of 8 ranks per lane");
     constexpr int G = 32 / LPN, RUN = kBatch / G, L = NIN - 1;
     static_assert(L >= 1 && RUN % ZA == 0, "factored path shape");
@@ -514,7 +543,7 @@ __device__ __forceinline__ void fiber_batch(const WarpStage<NIN>& st, int g, con
 #pragma unroll
         for (int a = 0; a < ZA; ++a) {
             r[a] = st.get(j0 + u + a);
-            z[a].load(fl[L] + (uint64_t)(uint32_t)r[a].idx(L) * R);
+            z[a].load(fl[L] + frow(p, L, r[a].idx(L)) * R);
         }
 #pragma unroll
         for (int a = 0; a < ZA; ++a) {
@@ -531,7 +560,7 @@ __device__ __forceinline__ void fiber_batch(const WarpStage<NIN>& st, int g, con
             for (int l = 0; l < L; ++l)
                 if (ch[l]) {
                     cur[l] = r[a].idx(l);
-                    x[l].load(fl[l] + (uint64_t)(uint32_t)cur[l] * R);
+                    x[l].load(fl[l] + frow(p, l, cur[l]) * R);
                 }
             const unsigned long long vv = pk(r[a].val(), r[a].val());
 #pragma unroll
@@ -580,14 +609,14 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
 
     // rowptr window of 64 rows in two registers per lane: w0 = rowptr[rwb + lane], w1 = rowptr[rwb + 32 + lane]
     int rwb = row_s;
-    int w0 = __ldg(p.rowptr + rwb + lane);
-    int w1 = __ldg(p.rowptr + rwb + 32 + lane);
+    int w0 = __ldg(p.rowptr + checked_index(p.err, kCheckRowptr, rwb + lane, p.I + 1 + kPad, -1));
+    int w1 = __ldg(p.rowptr + checked_index(p.err, kCheckRowptr, rwb + 32 + lane, p.I + 1 + kPad, -1));
     auto rowptr_at = [&](int r) -> int { return __shfl_sync(0xffffffffu, w0, r - rwb); };
     auto ensure_window = [&](int r) {  // keep rows r and r+1 in w0; slide by 32 (next half prefetched)
         if (r + 1 - rwb >= 32) {
             rwb += 32;
             w0 = w1;
-            w1 = __ldg(p.rowptr + rwb + 32 + lane);
+            w1 = __ldg(p.rowptr + checked_index(p.err, kCheckRowptr, rwb + 32 + lane, p.I + 1 + kPad, -1));
         }
     };
 
@@ -601,7 +630,7 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
     for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
     float ao[RES ? VEC : 1];  // residual mode: output-mode factor row of row i
     if constexpr (RES) {
-        if (i < p.I) load_out_row<T, VEC>(p, __ldg(p.rows_L + i), q, ao);
+        if (i < p.I) load_out_row<T, VEC>(p, out_row(p, __ldg(p.rows_L + i)), q, ao);
     }
 
     auto flush = [&](int row) {
@@ -611,7 +640,7 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
         if (row == row_s && cont) {
             dst = p.part + ((int64_t)s * 2) * R + rq;  // head partial of a split row
         } else if (row < row_e) {
-            dst = p.out + (int64_t)__ldg(p.rows_L + row) * R + rq;  // complete row: written exactly once
+            dst = p.out + (int64_t)out_row(p, __ldg(p.rows_L + row)) * R + rq;  // complete row: written exactly once
             streaming = true;
         } else {
             dst = p.part + ((int64_t)s * 2 + 1) * R + rq;  // tail partial of a split row
@@ -648,7 +677,7 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
             rend = nz_e;
         }
         if constexpr (RES) {
-            if (i < p.I && rend > rstart) load_out_row<T, VEC>(p, __ldg(p.rows_L + i), q, ao);
+            if (i < p.I && rend > rstart) load_out_row<T, VEC>(p, out_row(p, __ldg(p.rows_L + i)), q, ao);
         }
     };
 
@@ -664,7 +693,7 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
         if (kb + kBatch < nz_e) prefetch_batch<NIN>(p, kb + kBatch, lane);  // next batch into L2
         if constexpr (!RES && Factored<T, VEC, NIN>::value) {
             if (kb >= nz_s && kb + kBatch <= nz_e && kb + kBatch <= rend) {  // the batch lies inside row i
-                if (active) fiber_batch<T, VEC, LPN, NIN, Factored<T, VEC, NIN>::ahead>(st, g, fl, R, acc);
+                if (active) fiber_batch<T, VEC, LPN, NIN, Factored<T, VEC, NIN>::ahead>(p, st, g, fl, R, acc);
                 continue;
             }
         }
@@ -683,7 +712,7 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
                             Raw<T, VEC> x[NIN];
 #pragma unroll
                             for (int n = 0; n < NIN; ++n)
-                                x[n].load(fl[n] + (uint64_t)(uint32_t)r.idx(n) * R);
+                                x[n].load(fl[n] + frow(p, n, r.idx(n)) * R);
                             Mac<T, VEC, NIN>::run(acc, r.val(), x);
                         }
                     }
@@ -697,7 +726,7 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
                             Raw<T, VEC> x[NIN];
 #pragma unroll
                             for (int n = 0; n < NIN; ++n)
-                                x[n].load(fl[n] + (uint64_t)(uint32_t)r.idx(n) * R);
+                                x[n].load(fl[n] + frow(p, n, r.idx(n)) * R);
                             kr_row<T, VEC, NIN>(t, x);
                         } else {
 #pragma unroll
@@ -730,7 +759,7 @@ __device__ __forceinline__ void mttkrp_segment(const MttkrpParams& p, int s, War
                         Raw<T, VEC> x[NIN];
 #pragma unroll
                         for (int n = 0; n < NIN; ++n)
-                            x[n].load(fl[n] + (uint64_t)(uint32_t)r.idx(n) * R);
+                            x[n].load(fl[n] + frow(p, n, r.idx(n)) * R);
                         if constexpr (RES)
                             kr_row<T, VEC, NIN>(t[u], x);
                         else
@@ -787,9 +816,15 @@ __device__ __forceinline__ void mttkrp_short(const MttkrpParams& p, int t, WarpS
     const uint32_t R = (uint32_t)p.R;
     const int a = __ldg(p.seg_short + t), nr = __ldg(p.seg_short + t + 1) - a;  // nr <= 31
     const int my_rp = __ldg(p.rowptr_S + a + min(lane, nr));  // lane l: start of short row a+l; lane nr: end
-    const int my_id = lane < nr ? __ldg(p.rows_S + a + lane) : 0;
+    const int my_id = lane < nr ? out_row(p, __ldg(p.rows_S + a + lane)) : 0;
     const int k0 = __shfl_sync(0xffffffffu, my_rp, 0), k1 = __shfl_sync(0xffffffffu, my_rp, nr);
     const int kb = k0 & ~3;  // k1 - kb < kBatch by construction of the short segments
+#if AMPED_CHECKS
+    if (k1 - kb > kBatch || k0 > k1) {  // warp-uniform: the whole warp skips the segment
+        if (lane == 0) check_fail(p.err, kCheckShort, t, -1);
+        return;
+    }
+#endif
     if (k1 > k0) {
         StreamBatch<NIN> cur;
         load_batch<NIN>(p, kb + 4 * lane, cur);
@@ -816,7 +851,7 @@ __device__ __forceinline__ void mttkrp_short(const MttkrpParams& p, int t, WarpS
                         Raw<T, VEC> x[NIN];
 #pragma unroll
                         for (int n = 0; n < NIN; ++n)
-                            x[n].load(fl[n] + (uint64_t)(uint32_t)r.idx(n) * R);
+                            x[n].load(fl[n] + frow(p, n, r.idx(n)) * R);
                         Mac<T, VEC, NIN>::run(acc, r.val(), x);
                     }
                 }
@@ -836,7 +871,7 @@ __device__ __forceinline__ void mttkrp_short(const MttkrpParams& p, int t, WarpS
                 if (active && in) {
                     Raw<T, VEC> x[NIN];
 #pragma unroll
-                    for (int n = 0; n < NIN; ++n) x[n].load(fl[n] + (uint64_t)(uint32_t)r.idx(n) * R);
+                    for (int n = 0; n < NIN; ++n) x[n].load(fl[n] + frow(p, n, r.idx(n)) * R);
                     kr_row<T, VEC, NIN>(tt, x);
                 } else {
 #pragma unroll
@@ -917,7 +952,8 @@ __global__ void __launch_bounds__(256) sample_kernel(const SampleParams p) {
         const int kb = b * NB, kl = kb + 4 * q;
         int4 bi[NM];
 #pragma unroll
-        for (int n = 0; n < NM; ++n) bi[n] = ld_stream_i4(p.idx[n] + kl, pol);
+        for (int n = 0; n < NM; ++n)
+            bi[n] = ld_stream_i4(p.idx[n] + checked_index(p.err, kCheckStream, kl, (int)(p.stride - 3), n), pol);
         float res[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
         for (int j0 = 0; j0 < NB; j0 += CH) {
@@ -934,7 +970,8 @@ __global__ void __launch_bounds__(256) sample_kernel(const SampleParams p) {
                     float x[VEC];
                     if (active) {
                         Raw<T, VEC> raw;
-                        raw.load(static_cast<const T*>(p.fac[n]) + (int64_t)c * p.R + rq);
+                        raw.load(static_cast<const T*>(p.fac[n]) +
+                                 (int64_t)checked_index(p.err, kCheckCoord, c, p.fdim[n], n) * p.R + rq);
                         widen(raw, x);
                     } else {
 #pragma unroll
