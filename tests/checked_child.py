@@ -61,6 +61,24 @@ def valid():
             for n in range(c.nmodes):
                 assert oracle.row_error(grads[n].cpu().numpy(), ref[n], floor_frac=1e-6) <= 1e-4, (name, n)
             t.close()
+    # 6 and 8 modes (32-byte staged records, one nonzero per group step) with 16-bit factors
+    rng = np.random.default_rng(5)
+    for dims, R, dt, kind in (((30, 20, 12, 9, 7, 5), 16, torch.float32, "f32"),
+                              ((12, 10, 9, 8, 7, 6, 5, 4), 32, torch.float16, "f16")):
+        nnz = 20000
+        idx = np.stack([rng.integers(0, d, nnz) for d in dims], axis=1).astype(np.int32)
+        vals = rng.uniform(0, 1, nnz).astype(np.float32)
+        F = [rng.uniform(0, 1, (d, R)).astype(np.float32) for d in dims]
+        Fd = [torch.from_numpy(f).to(dt).cuda() for f in F]
+        Fo = F if kind == "f32" else [bits(f) for f in Fd]
+        t = amped.Tensor(dims, idx, vals)
+        outs = t.mttkrp_all(Fd)
+        for m in range(len(dims)):
+            assert oracle.row_error(outs[m].cpu().numpy(), oracle.mttkrp(dims, idx, vals, Fo, m, kind)) <= BAR, (dims, m)
+        m_gpu = t.cp_sample(Fd).cpu().numpy()
+        m_ref = oracle.cp_sample(dims, idx, Fo, kind)
+        assert np.max(np.abs(m_gpu - m_ref) / np.abs(m_ref)) <= BAR
+        t.close()
     print("checked build, valid inputs: ok")
 
 
