@@ -40,6 +40,19 @@ def test_exports_every_declared_symbol(L):
     assert L.amped_version().decode().startswith("amped-gb300")
 
 
+def test_checked_build_compiles_and_loads(tmp_path):
+    """The bounds-checked variant (-DAMPED_CHECKS=1) cross-compiles for sm_103a, exports the same
+    entry points and identifies itself; its kernels run in the GPU tests."""
+    from paper_2507_15121_gb300 import build
+    path = build.build(flags=["-DAMPED_CHECKS=1"], lib_path=str(tmp_path / "libamped_checked.so"),
+                       build_dir=str(tmp_path / "_build"))
+    C = ctypes.CDLL(path)
+    C.amped_version.restype = ctypes.c_char_p
+    assert C.amped_version().decode().endswith("(sm_103a, checked)")
+    for n in declared_functions():
+        assert hasattr(C, n), n
+
+
 def test_header_is_plain_c(tmp_path):
     """The boundary header compiles as strict ISO C (no C++ or CUDA types leak into it), and a C
     program that calls every declared entry point links against the library."""
